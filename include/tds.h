@@ -1,0 +1,180 @@
+/*
+ * tds.h -- C ABI of libtds, the GB300 (sm_103a) time step of the active-soil
+ * particle system from "A multiscale model of terrain dynamics for real-time
+ * earthmoving simulation" (Servin, Berglund, Nystedt).
+ *
+ * The mesoscale model of the paper takes the equipment's motion and contact
+ * interfaces as input (section "Mesoscale model": the macroscale model
+ * supplies the equipment's motion and contact forces at the terrain
+ * interface) together with the terrain surface heightfield (Eq. surface),
+ * and returns the soil motion (particles) and the body-particle contact force
+ * that is the source of the digging resistance (section "Microscale model").
+ * One call of tds_step performs, per time step, the three lines of
+ * Algorithm 1 that form the particle step:
+ *   "do collision detection"                            -> hash-grid broadphase,
+ *       particle-particle / particle-heightfield / particle-box contacts;
+ *   "solve the mesoscale MCP using iterative PGS solver" -> colour-sweep
+ *       projected Gauss-Seidel on the contact law of Eqs. signCoul1-3 with the
+ *       Hertz mapping and the SPOOK stepper (section "Contacting rigid
+ *       multibodies");
+ *   "update positions x_{i+1} = x_i + dt v_{i+1}".
+ *
+ * Conventions
+ *  - Every call returns a tds_status; nothing throws across the ABI.
+ *    tds_last_error() gives a message for the calling thread.
+ *  - Host pointers are caller-owned and only read (or written) during the
+ *    call. Units are SI. Arrays are structure-of-arrays of float32 indexed by
+ *    the particle id 0..n-1 given at creation.
+ *  - Device memory is owned by the scene: either allocated by the library
+ *    (workspace == NULL) or carved from one caller-provided device buffer of
+ *    tds_workspace_bytes() bytes (for example a torch tensor); the caller then
+ *    keeps it alive until tds_destroy_scene.
+ *  - All device work of a scene is issued on one CUDA stream (the caller's,
+ *    or the default stream when none is given). tds_step returns without
+ *    waiting for the GPU; the read calls and tds_synchronize wait.
+ *  - Errors detected on the device (capacity overflow, non-finite state,
+ *    a grid barrier that timed out) are latched in the scene and returned by
+ *    the next waiting call; the scene is then unusable until destroyed.
+ *  - Not thread-safe per scene; distinct scenes may be used concurrently.
+ */
+#ifndef TDS_H
+#define TDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDS_OK = 0,
+  TDS_ERR_INVALID_ARG = -1,     /* a NULL, negative or inconsistent argument */
+  TDS_ERR_CUDA = -2,            /* a CUDA runtime call failed (message says which) */
+  TDS_ERR_OOM = -3,             /* device allocation failed or workspace too small */
+  TDS_ERR_CAPACITY = -4,        /* more contacts or colours than the scene's capacity */
+  TDS_ERR_NONFINITE = -5,       /* a particle velocity or position became NaN/Inf */
+  TDS_ERR_BARRIER_TIMEOUT = -6, /* a grid-wide barrier waited longer than its limit */
+  TDS_ERR_STATE = -7            /* the scene already holds an error */
+} tds_status;
+
+typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1 } tds_warm_start;
+
+/* Scene description. All pointers are host pointers, read during
+ * tds_create_scene only.
+ *
+ * Particles (section "Particles"/"Mesoscale model", Eq. eqmotb): n spheres of
+ *   radius r, density rho: m = rho 4/3 pi r^3, I = 2/5 m r^2.
+ * Contact law (Eqs. signCoul1-3, Hertz mapping): Young's modulus E, Poisson
+ *   ratio nu, friction mu_t (mu_tool against the tool), rolling resistance
+ *   mu_r, particle cohesion c_p [Pa]. With c_p > 0 a contact exists while the
+ *   gap is below delta_c = 0.025 (r_a + r_b) and can pull with an impulse of
+ *   at most dt c_p pi rbar^2 (rbar = 2 r_a r_b / (r_a + r_b); r_a for walls
+ *   and terrain; tool contacts have no cohesion).
+ * Heightfield (Eq. surface, linearly interpolated): (hf_nx+1)*(hf_ny+1)
+ *   heights h[j*(hf_nx+1)+i] at (hf_x0 + i*hf_cell, hf_y0 + j*hf_cell), each
+ *   cell split into two triangles by the diagonal (i+1,j)-(i,j+1).
+ *   hf_nx == 0 disables the terrain.
+ * Walls: n_walls static boxes, 10 floats each: centre[3], unit quaternion
+ *   (w,x,y,z)[4], half extents[3], in the world frame.
+ * Tool: n_tool_boxes boxes in the tool frame (same 10-float layout); the
+ *   tool's pose and velocity come from tds_set_tool_pose. At most
+ *   TDS_MAX_BOXES walls + tool boxes in total.
+ * Solver (SPOOK, tau_n = 2 dt; PGS): time step dt, gravity, sweeps per step
+ *   (max_iters). tol > 0 switches to residual mode: stop when the
+ *   diagonally scaled natural-map residual is <= tol, checked every
+ *   residual_every sweeps, at most max_iters sweeps.
+ * Capacity: contacts_per_particle (0 = 10) bounds the contact count by
+ *   contacts_per_particle * n; exceeding it is TDS_ERR_CAPACITY.
+ * Broadphase domain: particles are binned in a uniform grid over the box
+ *   [domain_lo, domain_hi]; particles outside it still collide correctly
+ *   (they fall into the border cells). A zero box lets the library choose it
+ *   from the particles, heightfield and walls.
+ */
+#define TDS_MAX_BOXES 24
+
+typedef struct {
+  uint32_t n;
+  const float *x, *y, *z;      /* positions [m] */
+  const float *vx, *vy, *vz;   /* velocities [m/s] (NULL: zero) */
+  const float *wx, *wy, *wz;   /* angular velocities [rad/s] (NULL: zero) */
+  const float *radius;         /* [m] */
+  float density, young, poisson;
+  float mu_t, mu_r, cohesion, mu_tool;
+  uint32_t hf_nx, hf_ny;
+  float hf_x0, hf_y0, hf_cell;
+  const float *hf_heights;
+  uint32_t n_walls;
+  const float *walls;
+  uint32_t n_tool_boxes;
+  const float *tool_boxes;
+  float dt, gravity[3];
+  uint32_t max_iters;
+  float tol;
+  uint32_t residual_every;
+  int32_t warm_start;          /* tds_warm_start */
+  uint32_t contacts_per_particle;
+  float domain_lo[3], domain_hi[3];
+} tds_scene_desc;
+
+typedef struct tds_scene tds_scene; /* opaque */
+
+typedef struct {
+  uint32_t n_contacts, n_pp, n_static, n_colours, iterations;
+  float residual;              /* residual of the final impulses (residual mode), else -1 */
+  uint64_t steps;              /* steps taken since creation */
+} tds_step_stats;
+
+/* Bytes of device workspace a scene with this description needs. */
+tds_status tds_workspace_bytes(const tds_scene_desc *desc, uint64_t *bytes);
+
+/* Create a scene: validates desc, uploads the particle state and geometry.
+ * workspace: NULL (the library allocates with cudaMalloc) or a device
+ * pointer to at least tds_workspace_bytes() bytes, 256-byte aligned.
+ * stream: a cudaStream_t, or NULL for the default stream. */
+tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace,
+                            uint64_t workspace_bytes, void *stream, tds_scene **out);
+
+/* Pose (position, unit quaternion w,x,y,z) and velocity (linear, angular,
+ * world frame) of the kinematic tool for the following steps (Algorithm 1:
+ * the equipment's state comes from the macroscale model). The pose is held
+ * fixed during a step; its velocity enters the contact rows. */
+tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[4],
+                             const float linvel[3], const float angvel[3]);
+
+/* Advance nsteps time steps (asynchronous). */
+tds_status tds_step(tds_scene *s, uint32_t nsteps);
+
+/* Wait for the scene's stream; returns a latched device error, if any. */
+tds_status tds_synchronize(tds_scene *s);
+
+/* Copy the particle state to host arrays of n floats (any pointer may be
+ * NULL to skip it). n must equal the scene's particle count. Waits. */
+tds_status tds_read_particles(tds_scene *s, float *x, float *y, float *z, float *vx,
+                              float *vy, float *vz, float *wx, float *wy, float *wz,
+                              uint32_t n);
+
+/* Force [N] and torque about the tool origin [N m] exerted by the soil on the
+ * tool during the last step (impulses / dt). Waits. */
+tds_status tds_read_tool_force(tds_scene *s, float force[3], float torque[3]);
+
+/* Contacts of the last step, at most cap of them, in no particular order:
+ * key = (a << 32) | b for particles a < b, (a << 32) | 0x80000000 | s for
+ * particle a against static surface s (0 heightfield, 1.. walls, then tool
+ * boxes); lam = 7 floats per contact: normal impulse, tangent impulse
+ * (world frame, 3), rolling impulse (3) [N s]; colour = its colour.
+ * *count receives the total. Waits. */
+tds_status tds_read_contacts(tds_scene *s, uint64_t *keys, float *lam, uint32_t *colour,
+                             uint32_t cap, uint32_t *count);
+
+/* Statistics of the last step. Waits. */
+tds_status tds_get_stats(tds_scene *s, tds_step_stats *out);
+
+void tds_destroy_scene(tds_scene *s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *tds_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,594 @@
+// tds_api.cu -- host side of the C ABI declared in include/tds.h: scene
+// creation and workspace layout, per-step orchestration of the kernels on the
+// scene's stream, and the read calls.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tds_internal.cuh"
+
+// launchers (tds_contacts.cu, tds_colour.cu, tds_solve.cu)
+void tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st);
+void tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st);
+void tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
+                          int coop_threads, cudaStream_t st);
+void tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
+cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
+                           uint32_t every, int apply_warm, int blocks, cudaStream_t st);
+void tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
+void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
+const void *tds_pgs_kernel();
+const void *tds_colour_kernel();
+
+namespace {
+
+thread_local std::string g_err;
+
+tds_status fail(tds_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(TDS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+// Rotation matrix (row-major, world = R local) of a quaternion (w, x, y, z),
+// normalised in FP64. Together with the composition in compose_boxes this is
+// the box-geometry contract: FP64 evaluation in exactly this order, rounded to
+// FP32 before the contact predicate reads it.
+void quat_to_matrix(const float q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  double s = 1.0 / std::sqrt(((w * w + x * x) + y * y) + z * z);
+  w *= s; x *= s; y *= s; z *= s;
+  R[0] = 1.0 - 2.0 * (y * y + z * z);
+  R[1] = 2.0 * (x * y - w * z);
+  R[2] = 2.0 * (x * z + w * y);
+  R[3] = 2.0 * (x * y + w * z);
+  R[4] = 1.0 - 2.0 * (x * x + z * z);
+  R[5] = 2.0 * (y * z - w * x);
+  R[6] = 2.0 * (x * z - w * y);
+  R[7] = 2.0 * (y * z + w * x);
+  R[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+struct Sizes {
+  uint32_t n, cap, ncells, ntiles, hf_words;
+  int gnx, gny, gnz;
+  float lo[3], cell;
+};
+
+}  // namespace
+
+struct tds_scene {
+  tds_scene_desc desc;
+  Sizes sz;
+  StepConsts k;
+  DevPtrs d;
+  cudaStream_t st = nullptr;
+  void *mem = nullptr;
+  bool owns = false;
+  bool have_prev = false;
+  std::vector<float> walls, tool_boxes;
+  float tool_pos[3] = {0, 0, 0}, tool_quat[4] = {1, 0, 0, 0}, tool_vel[3] = {0, 0, 0},
+        tool_angvel[3] = {0, 0, 0};
+  int pgs_blocks = 1, colour_blocks = 1;
+  uint64_t steps = 0;
+  tds_status latched = TDS_OK;
+  std::vector<float> host_stage;
+};
+
+namespace {
+
+tds_status validate(const tds_scene_desc *d) {
+  if (!d) return fail(TDS_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n == 0 || d->n >= 0x7FFFFFFFu) return fail(TDS_ERR_INVALID_ARG, "n must be in [1, 2^31)");
+  if (!d->x || !d->y || !d->z || !d->radius) return fail(TDS_ERR_INVALID_ARG, "positions and radii are required");
+  if (!(d->dt > 0.f)) return fail(TDS_ERR_INVALID_ARG, "dt must be > 0");
+  if (!(d->density > 0.f) || !(d->young > 0.f) || !(d->poisson >= 0.f && d->poisson < 0.5f))
+    return fail(TDS_ERR_INVALID_ARG, "density, young > 0 and 0 <= poisson < 0.5 required");
+  if (d->mu_t < 0.f || d->mu_r < 0.f || d->cohesion < 0.f || d->mu_tool < 0.f)
+    return fail(TDS_ERR_INVALID_ARG, "friction, rolling resistance and cohesion must be >= 0");
+  if (d->n_walls + d->n_tool_boxes > TDS_MAX_BOXES)
+    return fail(TDS_ERR_INVALID_ARG, "too many boxes (TDS_MAX_BOXES)");
+  if ((d->n_walls && !d->walls) || (d->n_tool_boxes && !d->tool_boxes))
+    return fail(TDS_ERR_INVALID_ARG, "box arrays missing");
+  if (d->hf_nx > 0 && (d->hf_ny == 0 || !d->hf_heights || !(d->hf_cell > 0.f)))
+    return fail(TDS_ERR_INVALID_ARG, "heightfield needs ny > 0, heights and cell > 0");
+  if (d->max_iters == 0) return fail(TDS_ERR_INVALID_ARG, "max_iters must be >= 1");
+  if (d->warm_start != TDS_WARM_COLD && d->warm_start != TDS_WARM_PREV)
+    return fail(TDS_ERR_INVALID_ARG, "warm_start must be TDS_WARM_COLD or TDS_WARM_PREV");
+  for (uint32_t i = 0; i < d->n; ++i)
+    if (!(d->radius[i] > 0.f) || !std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) ||
+        !std::isfinite(d->z[i]))
+      return fail(TDS_ERR_INVALID_ARG, "radii must be > 0 and positions finite");
+  return TDS_OK;
+}
+
+Sizes plan(const tds_scene_desc *d) {
+  Sizes s{};
+  s.n = d->n;
+  uint32_t per = d->contacts_per_particle ? d->contacts_per_particle : 10u;
+  uint64_t cap = (uint64_t)per * d->n + 64;
+  if (cap > 0x7FFFFFF0ull) cap = 0x7FFFFFF0ull;
+  s.cap = (uint32_t)cap;
+  s.ntiles = (s.cap + TDS_TILE - 1) / TDS_TILE;
+  float rmax = 0.f;
+  for (uint32_t i = 0; i < d->n; ++i) rmax = std::fmax(rmax, d->radius[i]);
+  // cell wider than any reach (2 rmax plus the cohesive band), with margin
+  s.cell = 2.0f * rmax * 1.025f * 1.02f;
+  float lo[3], hi[3];
+  bool given = false;
+  for (int a = 0; a < 3; ++a) given |= d->domain_hi[a] > d->domain_lo[a];
+  if (given) {
+    for (int a = 0; a < 3; ++a) { lo[a] = d->domain_lo[a]; hi[a] = d->domain_hi[a]; }
+  } else {
+    const float *xs[3] = {d->x, d->y, d->z};
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = hi[a] = xs[a][0];
+      for (uint32_t i = 1; i < d->n; ++i) {
+        lo[a] = std::fmin(lo[a], xs[a][i]);
+        hi[a] = std::fmax(hi[a], xs[a][i]);
+      }
+    }
+    for (uint32_t w = 0; w < d->n_walls; ++w) {  // inner faces of the walls bound the bed
+      const float *b = d->walls + 10 * w;
+      double R[9];
+      quat_to_matrix(b + 3, R);
+      for (int a = 0; a < 3; ++a) {
+        double ext = std::fabs(R[3 * a]) * b[7] + std::fabs(R[3 * a + 1]) * b[8] + std::fabs(R[3 * a + 2]) * b[9];
+        if (a < 2) {
+          lo[a] = std::fmin(lo[a], (float)(b[a] - ext));
+          hi[a] = std::fmax(hi[a], (float)(b[a] + ext));
+        }
+      }
+    }
+    float margin = 2.0f * s.cell;
+    for (int a = 0; a < 3; ++a) { lo[a] -= margin; hi[a] += margin; }
+    hi[2] += 0.25f * (hi[2] - lo[2]);
+  }
+  int dims[3];
+  for (;;) {
+    uint64_t tot = 1;
+    for (int a = 0; a < 3; ++a) {
+      dims[a] = (int)std::ceil((hi[a] - lo[a]) / s.cell);
+      if (dims[a] < 1) dims[a] = 1;
+      tot *= (uint64_t)dims[a];
+    }
+    if (tot <= (1ull << 26)) break;
+    s.cell *= 1.25f;  // coarser cells keep the grid bounded; correctness is unaffected
+  }
+  s.gnx = dims[0]; s.gny = dims[1]; s.gnz = dims[2];
+  s.ncells = (uint32_t)((uint64_t)dims[0] * dims[1] * dims[2]);
+  for (int a = 0; a < 3; ++a) s.lo[a] = lo[a];
+  s.hf_words = d->hf_nx > 0 ? (d->hf_nx + 1) * (d->hf_ny + 1) : 1;
+  return s;
+}
+
+size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) {
+  const uint32_t n = s.n, cap = s.cap;
+  d.pos = c.take<float4>(n); d.vel = c.take<float4>(n); d.ang = c.take<float4>(n);
+  d.pid = c.take<uint32_t>(n);
+  d.pos2 = c.take<float4>(n); d.vel2 = c.take<float4>(n); d.ang2 = c.take<float4>(n);
+  d.pid2 = c.take<uint32_t>(n);
+  d.cell_of = c.take<uint32_t>(n);
+  d.cell_count = c.take<uint32_t>(s.ncells + 1);
+  d.cell_start = c.take<uint32_t>(s.ncells + 1);
+  d.cell_cursor = c.take<uint32_t>(s.ncells);
+  d.perm = c.take<uint32_t>(n);
+  d.cnt = c.take<uint32_t>(n + 1);
+  d.cstart = c.take<uint32_t>(n + 1);
+  d.c_ab = c.take<uint2>(cap);
+  d.c_key = c.take<unsigned long long>(cap);
+  d.c_rn = c.take<float4>(cap); d.c_rq = c.take<float4>(cap);
+  d.c_rm = c.take<float2>(cap);
+  d.c_sv = c.take<float4>(cap); d.c_sw = c.take<float4>(cap);
+  d.c_la = c.take<float4>(cap); d.c_lb = c.take<float2>(cap);
+  d.inc_cnt = c.take<uint32_t>(n + 1); d.inc_start = c.take<uint32_t>(n + 1);
+  d.inc_cursor = c.take<uint32_t>(n); d.inc_list = c.take<uint32_t>(2 * (size_t)cap);
+  d.colour = c.take<uint8_t>(cap);
+  d.wait = c.take<int32_t>(cap);
+  d.frontier0 = c.take<uint32_t>(cap); d.frontier1 = c.take<uint32_t>(cap);
+  d.ntiles = s.ntiles;
+  d.tile_hist = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles);
+  d.tile_off = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles + 1);
+  d.bucket_start = c.take<uint32_t>(TDS_NBUCKETS + 1);
+  d.order = c.take<uint32_t>(cap);
+  d.p_ab = c.take<uint2>(cap);
+  d.p_rn = c.take<float4>(cap); d.p_rq = c.take<float4>(cap);
+  d.p_rm = c.take<float2>(cap);
+  d.p_sv = c.take<float4>(cap); d.p_sw = c.take<float4>(cap);
+  d.p_la = c.take<float4>(cap); d.p_lb = c.take<float2>(cap);
+  for (int b = 0; b < 2; ++b) {
+    d.prev_first[b] = c.take<uint32_t>(n);
+    d.prev_cnt[b] = c.take<uint32_t>(n);
+    d.prev_other[b] = c.take<uint32_t>(cap);
+    d.prev_l0[b] = c.take<float4>(cap);
+    d.prev_l1[b] = c.take<float4>(cap);
+  }
+  d.err = c.take<int32_t>(1);
+  d.ctr = c.take<uint32_t>(CTR_COUNT);
+  d.fscal = c.take<float>(FS_COUNT);
+  size_t nd = 2 * (size_t)pgs_blocks;
+  if (nd < 6 * 128) nd = 6 * 128;
+  d.dpart = c.take<double>(nd);
+  d.bar = c.take<uint32_t>(2);
+  size_t m = s.ncells;
+  if (m < n) m = n;
+  if (m < (size_t)TDS_NBUCKETS * s.ntiles) m = (size_t)TDS_NBUCKETS * s.ntiles;
+  d.scan_tmp = c.take<uint32_t>(tds_scan_tmp_words((uint32_t)m));
+  d.stage = c.take<float>(9 * (size_t)n);
+  d.tool_out = c.take<float>(6);
+  *hf = c.take<float>(s.hf_words);
+  return c.off + 256;
+}
+
+int pgs_blocks_for(uint32_t n, int max_coop) {
+  int b = (int)((n + 511) / 512);
+  if (b < 1) b = 1;
+  return b < max_coop ? b : max_coop;
+}
+
+void set_box(BoxF &B, const double R[9], const double c[3], const float h[3], int is_tool) {
+  for (int i = 0; i < 9; ++i) B.R[i] = (float)R[i];
+  for (int i = 0; i < 3; ++i) { B.c[i] = (float)c[i]; B.h[i] = h[i]; }
+  B.is_tool = is_tool;
+}
+
+// World-frame boxes for the current tool pose: walls as given, tool boxes
+// composed as R_w = R_T R_k, c_w = p_T + R_T c_k in FP64, then rounded.
+void compose_boxes(tds_scene *s) {
+  StepConsts &k = s->k;
+  k.n_walls = (int)s->desc.n_walls;
+  k.nb = (int)(s->desc.n_walls + s->desc.n_tool_boxes);
+  for (uint32_t w = 0; w < s->desc.n_walls; ++w) {
+    const float *b = s->walls.data() + 10 * w;
+    double R[9], c[3] = {b[0], b[1], b[2]};
+    quat_to_matrix(b + 3, R);
+    set_box(k.box[w], R, c, b + 7, 0);
+  }
+  double RT[9];
+  quat_to_matrix(s->tool_quat, RT);
+  for (uint32_t t = 0; t < s->desc.n_tool_boxes; ++t) {
+    const float *b = s->tool_boxes.data() + 10 * t;
+    double Rk[9], Rw[9], c[3];
+    quat_to_matrix(b + 3, Rk);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        Rw[3 * i + j] = (RT[3 * i + 0] * Rk[0 + j] + RT[3 * i + 1] * Rk[3 + j]) + RT[3 * i + 2] * Rk[6 + j];
+    for (int i = 0; i < 3; ++i) {
+      double off = (RT[3 * i + 0] * (double)b[0] + RT[3 * i + 1] * (double)b[1]) + RT[3 * i + 2] * (double)b[2];
+      c[i] = (double)s->tool_pos[i] + off;
+    }
+    set_box(k.box[s->desc.n_walls + t], Rw, c, b + 7, 1);
+  }
+  for (int i = 0; i < 3; ++i) {
+    k.tp[i] = s->tool_pos[i];
+    k.tv[i] = s->tool_vel[i];
+    k.tw[i] = s->tool_angvel[i];
+  }
+}
+
+tds_status check_latched(tds_scene *s) {
+  if (s->latched != TDS_OK) return fail(TDS_ERR_STATE, "scene holds an earlier error");
+  return TDS_OK;
+}
+
+const char *dev_err_text(int32_t e) {
+  switch (e) {
+    case DEV_ERR_CAPACITY: return "contact or colour capacity exceeded (raise contacts_per_particle)";
+    case DEV_ERR_NONFINITE: return "non-finite particle state";
+    case DEV_ERR_BARRIER: return "grid barrier wait exceeded its time limit";
+    default: return "device error";
+  }
+}
+
+tds_status sync_and_check(tds_scene *s) {
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  int32_t e = 0;
+  CUDA_TRY(cudaMemcpy(&e, s->d.err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    s->latched = (tds_status)e;
+    return fail((tds_status)e, dev_err_text(e));
+  }
+  return TDS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tds_last_error(void) { return g_err.c_str(); }
+
+tds_status tds_workspace_bytes(const tds_scene_desc *desc, uint64_t *bytes) {
+  tds_status v = validate(desc);
+  if (v != TDS_OK) return v;
+  if (!bytes) return fail(TDS_ERR_INVALID_ARG, "bytes is NULL");
+  Sizes s = plan(desc);
+  DevPtrs d{};
+  float *hf;
+  Carver c{nullptr};
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *bytes = carve(c, s, d, &hf, 64 * sms);
+  return TDS_OK;
+}
+
+tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_t workspace_bytes,
+                            void *stream, tds_scene **out) {
+  tds_status v = validate(desc);
+  if (v != TDS_OK) return v;
+  if (!out) return fail(TDS_ERR_INVALID_ARG, "out is NULL");
+  if (workspace && ((uintptr_t)workspace & 255u))
+    return fail(TDS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  *out = nullptr;
+  tds_scene *s = new tds_scene();
+  s->desc = *desc;
+  s->st = (cudaStream_t)stream;
+  s->sz = plan(desc);
+  if (desc->n_walls) s->walls.assign(desc->walls, desc->walls + 10 * desc->n_walls);
+  if (desc->n_tool_boxes) s->tool_boxes.assign(desc->tool_boxes, desc->tool_boxes + 10 * desc->n_tool_boxes);
+  int dev = 0, sms = 0, occ_pgs = 0, occ_col = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pgs, tds_pgs_kernel(), 256, 0);
+  if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_col, tds_colour_kernel(), 256, 0);
+  if (ce != cudaSuccess || occ_pgs < 1 || occ_col < 1) {
+    delete s;
+    return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
+  }
+  int max_pgs = sms * (occ_pgs < 4 ? occ_pgs : 4);
+  s->pgs_blocks = pgs_blocks_for(desc->n, max_pgs);
+  s->colour_blocks = sms * (occ_col < 2 ? occ_col : 2);
+  float *hf = nullptr;
+  Carver probe{nullptr};
+  DevPtrs tmp{};
+  size_t need = carve(probe, s->sz, tmp, &hf, 64 * sms);
+  if (workspace) {
+    if (workspace_bytes < need) {
+      delete s;
+      return fail(TDS_ERR_OOM, "workspace smaller than tds_workspace_bytes()");
+    }
+    s->mem = workspace;
+  } else {
+    if (cudaMalloc(&s->mem, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return fail(TDS_ERR_OOM, "cudaMalloc of the scene workspace failed");
+    }
+    s->owns = true;
+  }
+  Carver c{(char *)s->mem};
+  carve(c, s->sz, s->d, &hf, 64 * sms);
+  // constants
+  StepConsts &k = s->k;
+  std::memset(&k, 0, sizeof(k));
+  k.n = desc->n;
+  k.cap = s->sz.cap;
+  k.dt = desc->dt;
+  for (int i = 0; i < 3; ++i) k.g[i] = desc->gravity[i];
+  k.ups = 1.0f / (1.0f + 4.0f * (2.0f * desc->dt) / desc->dt);
+  double nu = desc->poisson, E = desc->young;
+  k.estar_pair = (float)(1.0 / (2.0 * (1.0 - nu * nu) / E));
+  k.estar_static = (float)(E / (1.0 - nu * nu));
+  k.mu_t = desc->mu_t; k.mu_tool = desc->mu_tool; k.mu_r = desc->mu_r;
+  k.cohesion = desc->cohesion;
+  k.cohesive = desc->cohesion > 0.f;
+  k.sig_t = 1e-9f / desc->dt;
+  k.sig_r = 1e-9f / desc->dt;
+  k.gx0 = s->sz.lo[0]; k.gy0 = s->sz.lo[1]; k.gz0 = s->sz.lo[2];
+  k.cell_inv = 1.0f / s->sz.cell;
+  k.gnx = s->sz.gnx; k.gny = s->sz.gny; k.gnz = s->sz.gnz;
+  k.hf_nx = (int)desc->hf_nx; k.hf_ny = (int)desc->hf_ny;
+  k.hf_x0 = desc->hf_x0; k.hf_y0 = desc->hf_y0; k.hf_cell = desc->hf_cell;
+  k.hf_h = hf;
+  compose_boxes(s);
+  // upload particle state: (x, r), (v, 1/m), (w, 1/I), ids
+  const uint32_t n = desc->n;
+  std::vector<float4> P(n), V(n), W(n);
+  std::vector<uint32_t> ids(n);
+  const double pi = 3.14159265358979323846;
+  for (uint32_t i = 0; i < n; ++i) {
+    double r = desc->radius[i];
+    double m = desc->density * 4.0 / 3.0 * pi * r * r * r;
+    double I = 0.4 * m * r * r;
+    P[i] = make_float4(desc->x[i], desc->y[i], desc->z[i], desc->radius[i]);
+    V[i] = make_float4(desc->vx ? desc->vx[i] : 0.f, desc->vy ? desc->vy[i] : 0.f,
+                       desc->vz ? desc->vz[i] : 0.f, (float)(1.0 / m));
+    W[i] = make_float4(desc->wx ? desc->wx[i] : 0.f, desc->wy ? desc->wy[i] : 0.f,
+                       desc->wz ? desc->wz[i] : 0.f, (float)(1.0 / I));
+    ids[i] = i;
+  }
+  auto cleanup_fail = [&](const std::string &msg) {
+    if (s->owns) cudaFree(s->mem);
+    delete s;
+    return fail(TDS_ERR_CUDA, msg);
+  };
+  if (cudaMemcpyAsync(s->d.pos, P.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
+      cudaMemcpyAsync(s->d.vel, V.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
+      cudaMemcpyAsync(s->d.ang, W.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
+      cudaMemcpyAsync(s->d.pid, ids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
+      (desc->hf_nx > 0 &&
+       cudaMemcpyAsync(hf, desc->hf_heights, sizeof(float) * s->sz.hf_words, cudaMemcpyHostToDevice, s->st)) ||
+      cudaMemsetAsync(s->d.err, 0, sizeof(int32_t), s->st) ||
+      cudaMemsetAsync(s->d.ctr, 0, sizeof(uint32_t) * CTR_COUNT, s->st) ||
+      cudaMemsetAsync(s->d.fscal, 0, sizeof(float) * FS_COUNT, s->st) ||
+      cudaMemsetAsync(s->d.tool_out, 0, sizeof(float) * 6, s->st) ||
+      cudaMemsetAsync(s->d.bucket_start, 0, sizeof(uint32_t) * (TDS_NBUCKETS + 1), s->st) ||
+      cudaStreamSynchronize(s->st)) {
+    cudaGetLastError();
+    return cleanup_fail("uploading the scene failed");
+  }
+  *out = s;
+  return TDS_OK;
+}
+
+tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[4],
+                             const float linvel[3], const float angvel[3]) {
+  if (!s || !pos || !quat || !linvel || !angvel) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  double qn = std::sqrt((double)quat[0] * quat[0] + (double)quat[1] * quat[1] +
+                        (double)quat[2] * quat[2] + (double)quat[3] * quat[3]);
+  if (!(qn > 1e-6)) return fail(TDS_ERR_INVALID_ARG, "quaternion has zero norm");
+  for (int i = 0; i < 3; ++i) {
+    if (!std::isfinite(pos[i]) || !std::isfinite(linvel[i]) || !std::isfinite(angvel[i]))
+      return fail(TDS_ERR_INVALID_ARG, "non-finite tool pose");
+    s->tool_pos[i] = pos[i];
+    s->tool_vel[i] = linvel[i];
+    s->tool_angvel[i] = angvel[i];
+  }
+  for (int i = 0; i < 4; ++i) s->tool_quat[i] = quat[i];
+  compose_boxes(s);
+  return TDS_OK;
+}
+
+tds_status tds_step(tds_scene *s, uint32_t nsteps) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  const tds_scene_desc &D = s->desc;
+  for (uint32_t it = 0; it < nsteps; ++it) {
+    DevPtrs &d = s->d;
+    tds_launch_broadphase(d, s->k, s->sz.ncells, s->st);
+    std::swap(d.pos, d.pos2);
+    std::swap(d.vel, d.vel2);
+    std::swap(d.ang, d.ang2);
+    std::swap(d.pid, d.pid2);
+    int use_prev = (D.warm_start == TDS_WARM_PREV) && s->have_prev;
+    tds_launch_narrowphase(d, s->k, use_prev, s->st);
+    tds_launch_predict(d, s->k, s->st);
+    tds_launch_colouring(d, s->sz.n, s->sz.cap, s->colour_blocks, 256, s->st);
+    CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev,
+                            s->pgs_blocks, s->st));
+    tds_launch_finish(d, s->k, s->sz.cap, s->st);
+    std::swap(d.prev_first[0], d.prev_first[1]);
+    std::swap(d.prev_cnt[0], d.prev_cnt[1]);
+    std::swap(d.prev_other[0], d.prev_other[1]);
+    std::swap(d.prev_l0[0], d.prev_l0[1]);
+    std::swap(d.prev_l1[0], d.prev_l1[1]);
+    s->have_prev = true;
+    s->steps++;
+  }
+  CUDA_TRY(cudaGetLastError());
+  return TDS_OK;
+}
+
+tds_status tds_synchronize(tds_scene *s) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  return sync_and_check(s);
+}
+
+tds_status tds_read_particles(tds_scene *s, float *x, float *y, float *z, float *vx, float *vy,
+                              float *vz, float *wx, float *wy, float *wz, uint32_t n) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (n != s->sz.n) return fail(TDS_ERR_INVALID_ARG, "n differs from the scene's particle count");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  tds_launch_stage(s->d, n, s->st);
+  float *outs[9] = {x, y, z, vx, vy, vz, wx, wy, wz};
+  for (int q = 0; q < 9; ++q)
+    if (outs[q])
+      CUDA_TRY(cudaMemcpyAsync(outs[q], s->d.stage + (size_t)q * n, sizeof(float) * n,
+                               cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+tds_status tds_read_tool_force(tds_scene *s, float force[3], float torque[3]) {
+  if (!s || !force || !torque) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  float buf[6];
+  CUDA_TRY(cudaMemcpyAsync(buf, s->d.tool_out, sizeof(buf), cudaMemcpyDeviceToHost, s->st));
+  tds_status r = sync_and_check(s);
+  if (r != TDS_OK) return r;
+  for (int i = 0; i < 3; ++i) { force[i] = buf[i]; torque[i] = buf[3 + i]; }
+  return TDS_OK;
+}
+
+tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
+  if (!s || !out) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  uint32_t ctr[CTR_COUNT];
+  float fs[FS_COUNT];
+  std::vector<uint32_t> bs(TDS_NBUCKETS + 1);
+  CUDA_TRY(cudaMemcpyAsync(ctr, s->d.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(fs, s->d.fscal, sizeof(fs), cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bucket_start, sizeof(uint32_t) * bs.size(),
+                           cudaMemcpyDeviceToHost, s->st));
+  tds_status r = sync_and_check(s);
+  if (r != TDS_OK) return r;
+  std::memset(out, 0, sizeof(*out));
+  out->n_contacts = ctr[CTR_NC];
+  uint32_t nst = 0;
+  for (int c = 0; c < TDS_MAX_COLOURS; ++c) nst += bs[2 * c + 2] - bs[2 * c + 1];
+  out->n_static = nst;
+  out->n_pp = ctr[CTR_NC] - nst;
+  out->n_colours = ctr[CTR_NCOL];
+  out->iterations = ctr[CTR_ITERS];
+  out->residual = fs[FS_RESID];
+  out->steps = s->steps;
+  return TDS_OK;
+}
+
+tds_status tds_read_contacts(tds_scene *s, uint64_t *keys, float *lam, uint32_t *colour,
+                             uint32_t cap, uint32_t *count) {
+  if (!s || !count) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  uint32_t nc = 0;
+  CUDA_TRY(cudaMemcpyAsync(&nc, s->d.ctr + CTR_NC, sizeof(nc), cudaMemcpyDeviceToHost, s->st));
+  tds_status r = sync_and_check(s);
+  if (r != TDS_OK) return r;
+  *count = nc;
+  uint32_t m = nc < cap ? nc : cap;
+  if (m == 0 || !s->have_prev) return TDS_OK;
+  std::vector<float4> l0(m), l1(m);
+  if (keys) CUDA_TRY(cudaMemcpyAsync(keys, s->d.c_key, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s->st));
+  if (colour) {
+    std::vector<uint8_t> col(m);
+    CUDA_TRY(cudaMemcpyAsync(col.data(), s->d.colour, m, cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaStreamSynchronize(s->st));
+    for (uint32_t i = 0; i < m; ++i) colour[i] = col[i];
+  }
+  if (lam) {
+    CUDA_TRY(cudaMemcpyAsync(l0.data(), s->d.prev_l0[0], sizeof(float4) * m, cudaMemcpyDeviceToHost, s->st));
+    CUDA_TRY(cudaMemcpyAsync(l1.data(), s->d.prev_l1[0], sizeof(float4) * m, cudaMemcpyDeviceToHost, s->st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  if (lam)
+    for (uint32_t i = 0; i < m; ++i) {
+      float *o = lam + 7 * (size_t)i;
+      o[0] = l0[i].x; o[1] = l0[i].y; o[2] = l0[i].z; o[3] = l0[i].w;
+      o[4] = l1[i].x; o[5] = l1[i].y; o[6] = l1[i].z;
+    }
+  return TDS_OK;
+}
+
+void tds_destroy_scene(tds_scene *s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  else cudaDeviceSynchronize();
+  if (s->owns && s->mem) cudaFree(s->mem);
+  delete s;
+}
+
+}  // extern "C"

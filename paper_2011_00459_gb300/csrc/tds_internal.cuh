@@ -1,0 +1,190 @@
+// tds_internal.cuh -- device-side types and helpers shared by the kernels of
+// libtds (the GB300 particle step). Nothing here is visible through the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tds.h"
+
+#define TDS_STATIC 0x80000000u
+#define TDS_NO_COLOUR 0xFFu
+#define TDS_MAX_COLOURS 128
+#define TDS_NBUCKETS (2 * TDS_MAX_COLOURS)  // (colour, static?) buckets
+#define TDS_TILE 2048                       // contacts per bucketing tile
+#define TDS_BARRIER_NS 2000000000ull        // 2 s limit on any grid-barrier wait
+
+// Error codes latched on the device (the tds_status values).
+#define DEV_ERR_CAPACITY (-4)
+#define DEV_ERR_NONFINITE (-5)
+#define DEV_ERR_BARRIER (-6)
+
+// A static box in the world frame, FP32 (walls first, then tool boxes).
+struct BoxF {
+  float c[3];
+  float R[9];  // row-major, world = R * local + c
+  float h[3];
+  int is_tool;
+};
+
+// Per-step constants, passed by value to every kernel.
+struct StepConsts {
+  uint32_t n;           // particles
+  uint32_t cap;         // contact capacity
+  float dt, g[3];
+  float ups;            // Upsilon = 1 / (1 + 4 tau / dt), tau = 2 dt
+  float estar_pair;     // [2 (1 - nu^2) / E]^-1
+  float estar_static;   // E / (1 - nu^2)
+  float mu_t, mu_tool, mu_r, cohesion;
+  int cohesive;
+  float sig_t, sig_r;   // gamma_t / dt, gamma_r / dt
+  // broadphase grid
+  float gx0, gy0, gz0, cell_inv;
+  int gnx, gny, gnz;
+  // heightfield
+  int hf_nx, hf_ny;
+  float hf_x0, hf_y0, hf_cell;
+  const float *hf_h;
+  // boxes
+  int nb, n_walls;
+  BoxF box[TDS_MAX_BOXES];
+  // tool motion (point velocity v_T + w_T x (x - p_T))
+  float tp[3], tv[3], tw[3];
+};
+
+// Device pointers of one scene (passed by value).
+struct DevPtrs {
+  // particles, slot order (re-sorted by cell every step)
+  float4 *pos, *vel, *ang;    // (x,y,z,r), (v, 1/m), (w, 1/I)
+  uint32_t *pid;
+  float4 *pos2, *vel2, *ang2; // reorder targets
+  uint32_t *pid2;
+  // grid
+  uint32_t *cell_of, *cell_count, *cell_start, *cell_cursor, *perm;
+  // contacts in owner order (owner = the particle with the smaller id)
+  uint32_t *cnt, *cstart;     // per slot (n + 1)
+  uint2 *c_ab;                // slot a, slot b | TDS_STATIC + surface id
+  unsigned long long *c_key;
+  float4 *c_rn, *c_rq;        // (n, la), (lb, q_n, Sigma_n, f_c)
+  float2 *c_rm;               // (mu, rbar mu_r)
+  float4 *c_sv, *c_sw;        // static side: point velocity, spin
+  float4 *c_la;               // initial impulses (n, t1, t2, r.x)
+  float2 *c_lb;               // (r.y, r.z)
+  // colouring
+  uint32_t *inc_cnt, *inc_start, *inc_cursor, *inc_list;
+  uint8_t *colour;
+  int32_t *wait;
+  uint32_t *frontier0, *frontier1;
+  // bucketing into colour order
+  uint32_t *tile_hist, *tile_off, *bucket_start, *order;
+  uint32_t ntiles;
+  // colour order (what the solver streams)
+  uint2 *p_ab;
+  float4 *p_rn, *p_rq;
+  float2 *p_rm;
+  float4 *p_sv, *p_sw;
+  float4 *p_la;
+  float2 *p_lb;
+  // warm-start memory by particle id: [0] read, [1] written this step
+  uint32_t *prev_first[2], *prev_cnt[2], *prev_other[2];
+  float4 *prev_l0[2], *prev_l1[2];
+  // scalars and scratch
+  int32_t *err;
+  uint32_t *ctr;              // see CTR_* below
+  float *fscal;               // see FS_* below
+  double *dpart;              // per-block partial sums
+  uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
+  uint32_t *scan_tmp;
+  float *stage;               // 9 n floats for reads
+  float *tool_out;            // 6 floats
+};
+
+enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
+       CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_COUNT = 16 };
+enum { FS_RESID = 0, FS_COUNT = 4 };
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Orthonormal tangent basis of a unit normal, branch-free (Duff, Burgess,
+// Christensen, Hery, Kensler, Liani, Villemin, "Building an Orthonormal
+// Basis, Revisited", JCGT 6(1), 2017). The 2-D tangent update is invariant
+// under the choice of basis, since its effective mass is isotropic.
+__device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
+  float sgn = copysignf(1.0f, n.z);
+  float a = -1.0f / (sgn + n.z);
+  float b = n.x * n.y * a;
+  t1 = make_float3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
+  t2 = make_float3(b, sgn + n.y * n.y * a, -n.y);
+}
+
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): the colouring
+// priority of a contact key. A bijection, so distinct keys never tie.
+__device__ __forceinline__ unsigned long long priority(unsigned long long key) {
+  unsigned long long z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
+  atomicCAS(err, 0, code);
+}
+
+// Grid-wide barrier for cooperative (co-resident) launches: arrival counter
+// plus generation word, bounded wait. Returns false (and latches
+// DEV_ERR_BARRIER) if the wait ran past TDS_BARRIER_NS or another block
+// already failed; the caller must then return.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t *vgen = bar + 1;
+    uint32_t gen = *vgen;
+    __threadfence();
+    uint32_t arrived = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (*vgen == gen) {
+        if (((++spins) & 63u) == 0) {
+          if (*(volatile int32_t *)err != 0) { ok = 0; break; }
+          if (global_ns() - t0 > TDS_BARRIER_NS) {
+            latch_error(err, DEV_ERR_BARRIER);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int32_t *)err != 0) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Host-side launchers implemented in the .cu files.
+void tds_scan_exclusive(const uint32_t *in, uint32_t *out, uint32_t m, uint32_t *tmp,
+                        cudaStream_t st);
+size_t tds_scan_tmp_words(uint32_t m);

@@ -1,0 +1,264 @@
+"""Python binding of libtds (argument marshalling only).
+
+Every step of the particle time step runs in the CUDA library behind the C ABI
+of ``include/tds.h``; this module converts scene dictionaries (see
+``scenes.py``) into ``tds_scene_desc``, provides device memory and the CUDA
+stream through PyTorch, and copies results back. There is no CPU fallback:
+without the built library (or without a GPU) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtds.so")
+
+TDS_OK = 0
+STATUS = {0: "TDS_OK", -1: "TDS_ERR_INVALID_ARG", -2: "TDS_ERR_CUDA", -3: "TDS_ERR_OOM",
+          -4: "TDS_ERR_CAPACITY", -5: "TDS_ERR_NONFINITE", -6: "TDS_ERR_BARRIER_TIMEOUT",
+          -7: "TDS_ERR_STATE"}
+MAX_BOXES = 24
+STATIC_BIT = 0x80000000
+
+EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds_step",
+            "tds_synchronize", "tds_read_particles", "tds_read_tool_force", "tds_read_contacts",
+            "tds_get_stats", "tds_destroy_scene", "tds_last_error"]
+
+
+class TdsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_f = ctypes.c_float
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_uint32),
+        ("x", _fp), ("y", _fp), ("z", _fp),
+        ("vx", _fp), ("vy", _fp), ("vz", _fp),
+        ("wx", _fp), ("wy", _fp), ("wz", _fp),
+        ("radius", _fp),
+        ("density", _f), ("young", _f), ("poisson", _f),
+        ("mu_t", _f), ("mu_r", _f), ("cohesion", _f), ("mu_tool", _f),
+        ("hf_nx", ctypes.c_uint32), ("hf_ny", ctypes.c_uint32),
+        ("hf_x0", _f), ("hf_y0", _f), ("hf_cell", _f), ("hf_heights", _fp),
+        ("n_walls", ctypes.c_uint32), ("walls", _fp),
+        ("n_tool_boxes", ctypes.c_uint32), ("tool_boxes", _fp),
+        ("dt", _f), ("gravity", _f * 3),
+        ("max_iters", ctypes.c_uint32), ("tol", _f), ("residual_every", ctypes.c_uint32),
+        ("warm_start", ctypes.c_int32), ("contacts_per_particle", ctypes.c_uint32),
+        ("domain_lo", _f * 3), ("domain_hi", _f * 3),
+    ]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("n_contacts", ctypes.c_uint32), ("n_pp", ctypes.c_uint32),
+                ("n_static", ctypes.c_uint32), ("n_colours", ctypes.c_uint32),
+                ("iterations", ctypes.c_uint32), ("residual", ctypes.c_float),
+                ("steps", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtds.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise TdsError(-2, f"{LIB_PATH} is missing: build it with paper_2011_00459_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp = ctypes.c_void_p
+        L.tds_workspace_bytes.argtypes = [ctypes.POINTER(SceneDesc), ctypes.POINTER(ctypes.c_uint64)]
+        L.tds_create_scene.argtypes = [ctypes.POINTER(SceneDesc), vp, ctypes.c_uint64, vp,
+                                       ctypes.POINTER(vp)]
+        L.tds_set_tool_pose.argtypes = [vp, _fp, _fp, _fp, _fp]
+        L.tds_step.argtypes = [vp, ctypes.c_uint32]
+        L.tds_synchronize.argtypes = [vp]
+        L.tds_read_particles.argtypes = [vp] + [vp] * 9 + [ctypes.c_uint32]
+        L.tds_read_tool_force.argtypes = [vp, _fp, _fp]
+        L.tds_read_contacts.argtypes = [vp, vp, vp, vp, ctypes.c_uint32,
+                                        ctypes.POINTER(ctypes.c_uint32)]
+        L.tds_get_stats.argtypes = [vp, ctypes.POINTER(StepStats)]
+        L.tds_destroy_scene.argtypes = [vp]
+        L.tds_destroy_scene.restype = None
+        L.tds_last_error.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("tds_destroy_scene", "tds_last_error"):
+                getattr(L, name).restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != TDS_OK:
+        raise TdsError(status, lib().tds_last_error().decode())
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(_fp)
+
+
+def _vec(a, n):
+    return (_f * n)(*[float(v) for v in a])
+
+
+class Scene:
+    """One simulated bed on the current CUDA device.
+
+    ``workspace="torch"`` carves all device memory from one torch uint8 tensor;
+    ``"library"`` lets libtds cudaMalloc it. The CUDA stream is torch's current
+    stream unless ``stream`` (a ``torch.cuda.Stream``) is given.
+    """
+
+    def __init__(self, scene: dict, stream=None, workspace: str = "torch",
+                 contacts_per_particle: int = 0, domain=None, **override):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise TdsError(-2, "no CUDA device")
+        s = dict(scene)
+        s.update(override)
+        x = _f32(s["x"]).reshape(-1, 3)
+        n = x.shape[0]
+        keep = []
+
+        def col(a, k):
+            c = np.ascontiguousarray(a[:, k])
+            keep.append(c)
+            return _fptr(c)
+
+        v = _f32(s.get("v", np.zeros((n, 3)))).reshape(n, 3)
+        w = _f32(s.get("w", np.zeros((n, 3)))).reshape(n, 3)
+        r = _f32(s["r"]).reshape(n)
+        keep.append(r)
+        d = SceneDesc()
+        d.n = n
+        d.x, d.y, d.z = col(x, 0), col(x, 1), col(x, 2)
+        d.vx, d.vy, d.vz = col(v, 0), col(v, 1), col(v, 2)
+        d.wx, d.wy, d.wz = col(w, 0), col(w, 1), col(w, 2)
+        d.radius = _fptr(r)
+        d.density, d.young, d.poisson = s["density"], s["young"], s["poisson"]
+        d.mu_t, d.mu_r, d.cohesion = s["mu_t"], s["mu_r"], s["cohesion"]
+        d.mu_tool = s.get("mu_tool", s["mu_t"])
+        hf = s.get("hf")
+        if hf is not None:
+            h = _f32(hf["h"]).reshape(-1)
+            keep.append(h)
+            d.hf_nx, d.hf_ny = hf["nx"], hf["ny"]
+            d.hf_x0, d.hf_y0, d.hf_cell = hf["x0"], hf["y0"], hf["cell"]
+            d.hf_heights = _fptr(h)
+        walls = _f32(s.get("walls", np.zeros((0, 10)))).reshape(-1, 10)
+        boxes = _f32(s.get("tool_boxes", np.zeros((0, 10)))).reshape(-1, 10)
+        keep += [walls, boxes]
+        d.n_walls, d.walls = walls.shape[0], _fptr(walls)
+        d.n_tool_boxes, d.tool_boxes = boxes.shape[0], _fptr(boxes)
+        d.dt = s["dt"]
+        for i in range(3):
+            d.gravity[i] = s["gravity"][i]
+        d.max_iters = int(s["iters"])
+        d.tol = float(s.get("tol", 0.0))
+        d.residual_every = int(s.get("residual_every", 10))
+        d.warm_start = int(s.get("warm_start", 1))
+        d.contacts_per_particle = int(contacts_per_particle)
+        if domain is not None:
+            for i in range(3):
+                d.domain_lo[i], d.domain_hi[i] = domain[0][i], domain[1][i]
+        self.n = n
+        self.desc = d
+        self._keep = keep
+        L = lib()
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._ws = None
+        ws_ptr, ws_bytes = None, 0
+        if workspace == "torch":
+            nb = ctypes.c_uint64()
+            _check(L.tds_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)))
+            self._ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device="cuda")
+            base = self._ws.data_ptr()
+            ws_ptr = (base + 255) & ~255
+            ws_bytes = int(nb.value)
+        h = ctypes.c_void_p()
+        _check(L.tds_create_scene(ctypes.byref(d), ws_ptr, ws_bytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+        if "tool" in s and s["tool"] is not None:
+            self.set_tool_pose(s["tool"])
+
+    # -- calls ---------------------------------------------------------------
+    def set_tool_pose(self, tool: dict):
+        _check(lib().tds_set_tool_pose(self.h, _vec(tool["pos"], 3), _vec(tool["quat"], 4),
+                                       _vec(tool["vel"], 3), _vec(tool["angvel"], 3)))
+
+    def step(self, nsteps: int = 1):
+        _check(lib().tds_step(self.h, nsteps))
+
+    def synchronize(self):
+        _check(lib().tds_synchronize(self.h))
+
+    def read_particles(self, out=None) -> dict:
+        """x, v, w as (n, 3) float32 numpy arrays. ``out`` may give nine
+        preallocated float32 host buffers (e.g. pinned torch tensors' numpy
+        views) to copy into."""
+        n = self.n
+        bufs = out if out is not None else [np.empty(n, np.float32) for _ in range(9)]
+        ptrs = [ctypes.c_void_p(b.ctypes.data) if b is not None else None for b in bufs]
+        _check(lib().tds_read_particles(self.h, *ptrs, n))
+        if out is not None:
+            return {}
+        return {"x": np.stack(bufs[0:3], 1), "v": np.stack(bufs[3:6], 1), "w": np.stack(bufs[6:9], 1)}
+
+    def read_positions_into(self, x, y, z):
+        _check(lib().tds_read_particles(self.h, ctypes.c_void_p(x.ctypes.data),
+                                        ctypes.c_void_p(y.ctypes.data), ctypes.c_void_p(z.ctypes.data),
+                                        None, None, None, None, None, None, self.n))
+
+    def read_tool_force(self):
+        f = (_f * 3)()
+        t = (_f * 3)()
+        _check(lib().tds_read_tool_force(self.h, f, t))
+        return np.array(f[:], np.float64), np.array(t[:], np.float64)
+
+    def read_contacts(self) -> dict:
+        """The last step's contacts sorted by key: keys (uint64), lam (m, 7)
+        float32 [normal, tangent world xyz, rolling xyz], colour (uint32)."""
+        cnt = ctypes.c_uint32()
+        _check(lib().tds_read_contacts(self.h, None, None, None, 0, ctypes.byref(cnt)))
+        m = int(cnt.value)
+        keys = np.zeros(m, np.uint64)
+        lam = np.zeros((m, 7), np.float32)
+        col = np.zeros(m, np.uint32)
+        _check(lib().tds_read_contacts(self.h, ctypes.c_void_p(keys.ctypes.data),
+                                       ctypes.c_void_p(lam.ctypes.data),
+                                       ctypes.c_void_p(col.ctypes.data), m, ctypes.byref(cnt)))
+        o = np.argsort(keys, kind="stable")
+        return {"keys": keys[o], "lam": lam[o], "colour": col[o]}
+
+    def stats(self) -> dict:
+        st = StepStats()
+        _check(lib().tds_get_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in StepStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tds_destroy_scene(self.h)
+            self.h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

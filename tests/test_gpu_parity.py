@@ -1,0 +1,129 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs: contact key sets and colourings bit-exact, impulses within 1e-4
+relative (aggregate 2-norm over all rows), positions within 1e-6 m."""
+import numpy as np
+import pytest
+
+from paper_2011_00459_gb300 import scenes as S
+from tests.parity_cases import packed_scene, rel_impulse_error
+
+pytestmark = pytest.mark.gpu
+
+IMPULSE_TOL = 1e-4
+POS_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def tds():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2011_00459_gb300 import build, tds
+
+    build.build()
+    return tds
+
+
+def one_step(tds, orc, scene, **gpu_kw):
+    st = orc.State(scene)
+    ref = orc.step(scene, st)
+    g = tds.Scene(scene, **gpu_kw)
+    g.step(1)
+    out = g.read_contacts()
+    parts = g.read_particles()
+    stats = g.stats()
+    f, t = g.read_tool_force()
+    g.close()
+    return ref, st, out, parts, stats, (f, t)
+
+
+def assert_parity(ref, st, out, parts, stats):
+    assert stats["n_contacts"] == ref["n_contacts"]
+    assert np.array_equal(out["keys"], ref["keys"])
+    assert np.array_equal(out["colour"].astype(np.int64), ref["colour"].astype(np.int64))
+    assert stats["n_colours"] == ref["n_colours"]
+    if ref["n_contacts"]:
+        assert rel_impulse_error(out["lam"], ref["lam"]) <= IMPULSE_TOL
+    assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= POS_TOL
+
+
+@pytest.mark.parametrize("n,seed,cohesion,mu_r", [
+    (3000, 0, 1000.0, 0.1),     # several bucketing tiles and a ragged tail, cohesive
+    (2500, 1, 0.0, 0.3),        # cohesionless, strong rolling resistance
+    (777, 2, 5000.0, 0.0),      # odd size, no rolling resistance
+])
+def test_one_step_parity_packed(tds, orc, n, seed, cohesion, mu_r):
+    scene = packed_scene(n, seed, cohesion=cohesion, mu_r=mu_r, iters=50)
+    ref, st, out, parts, stats, (f, t) = one_step(tds, orc, scene)
+    assert ref["n_pp"] > n and ref["n_static"] > 0
+    assert_parity(ref, st, out, parts, stats)
+    np.testing.assert_allclose(f, ref["tool_force"], rtol=1e-3, atol=1e-3 * (1 + np.abs(ref["tool_force"]).max()))
+    np.testing.assert_allclose(t, ref["tool_torque"], rtol=1e-3, atol=1e-3 * (1 + np.abs(ref["tool_torque"]).max()))
+
+
+def test_one_step_parity_library_workspace(tds, orc):
+    scene = packed_scene(1200, 3, iters=20)
+    ref, st, out, parts, stats, _ = one_step(tds, orc, scene, workspace="library")
+    assert_parity(ref, st, out, parts, stats)
+
+
+def test_residual_mode_parity(tds, orc):
+    scene = packed_scene(1500, 4, iters=400, tol=1e-3)
+    ref, st, out, parts, stats, _ = one_step(tds, orc, scene)
+    assert np.array_equal(out["keys"], ref["keys"])
+    assert stats["residual"] <= 1e-3 and ref["residual"] <= 1e-3
+    # same stopping sweep within one check period
+    assert abs(stats["iterations"] - ref["iterations"]) <= 5
+    assert rel_impulse_error(out["lam"], ref["lam"]) <= 1e-3
+
+
+def test_free_fall_without_contacts(tds, orc):
+    scene = S.with_particles(S.base_params(iters=5), [[0.1, 0.2, 5.0], [3.0, 0.0, 1.0]],
+                             [0.05, 0.04], [[0.3, -0.2, 1.5], [0.0, 0.0, 0.0]])
+    ref, st, out, parts, stats, _ = one_step(tds, orc, scene)
+    assert ref["n_contacts"] == 0 and stats["n_contacts"] == 0 and stats["n_colours"] == 0
+    assert np.abs(parts["x"] - st.x).max() <= POS_TOL
+    assert np.abs(parts["v"] - st.v).max() <= 1e-6
+
+
+def test_particles_outside_the_grid_domain(tds, orc):
+    """Particles beyond the broadphase box fall into its border cells and
+    still find every contact."""
+    scene = packed_scene(600, 6, iters=20)
+    ref, st, out, parts, stats, _ = one_step(tds, orc, scene, domain=((0.1, 0.1, 0.1), (0.2, 0.2, 0.2)))
+    assert_parity(ref, st, out, parts, stats)
+
+
+def test_multi_step_warm_start(tds, orc):
+    """Five steps with previous-step warm start: contact sets agree up to
+    borderline pairs, impulses of common contacts within 1e-3, positions
+    within 1e-5 m (FP32 state vs FP64 state)."""
+    scene = packed_scene(1500, 7, iters=30)
+    st = orc.State(scene)
+    g = tds.Scene(scene)
+    for _ in range(5):
+        ref = orc.step(scene, st)
+        g.step(1)
+    out = g.read_contacts()
+    parts = g.read_particles()
+    g.close()
+    common, ia, ib = np.intersect1d(out["keys"], ref["keys"], return_indices=True)
+    assert len(common) >= 0.999 * max(len(out["keys"]), len(ref["keys"]))
+    assert rel_impulse_error(out["lam"][ia], ref["lam"][ib]) <= 1e-3
+    assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= 1e-5
+
+
+def test_steps_are_deterministic(tds):
+    scene = packed_scene(2000, 8, iters=20)
+    res = []
+    for _ in range(2):
+        g = tds.Scene(scene)
+        g.step(3)
+        res.append((g.read_particles(), g.read_contacts(), g.read_tool_force()))
+        g.close()
+    (pa, ca, fa), (pb, cb, fb) = res
+    for k in ("x", "v", "w"):
+        assert np.array_equal(pa[k], pb[k])
+    assert np.array_equal(ca["lam"], cb["lam"])
+    assert np.array_equal(fa[0], fb[0])
