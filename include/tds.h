@@ -120,8 +120,16 @@ typedef struct tds_scene tds_scene; /* opaque */
 
 typedef struct {
   uint32_t n_contacts, n_pp, n_static, n_colours, iterations;
-  float residual;              /* residual of the final impulses (residual mode), else -1 */
+  float residual;              /* natural-map residual of the final impulses */
   uint64_t steps;              /* steps taken since creation */
+  uint64_t kernel_launches;    /* kernels launched since creation */
+  uint32_t timed_steps;        /* steps timed since the previous tds_get_stats */
+  float phase_ms[5];           /* summed over those steps: broadphase, narrowphase
+                                  (contacts, rows, warm start), colouring, PGS solve,
+                                  finish (write-back, tool force, integration) */
+  /* sums over the steps since the previous tds_get_stats (which resets them):
+     sweeps x particle-pair contacts, sweeps x static contacts, contacts, steps */
+  uint64_t sweep_contacts_pp, sweep_contacts_static, sum_contacts, solved_steps;
 } tds_step_stats;
 
 /* Bytes of device workspace a scene with this description needs. */
@@ -140,6 +148,10 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace,
  * fixed during a step; its velocity enters the contact rows. */
 tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[4],
                              const float linvel[3], const float angvel[3]);
+
+/* Change the solver settings for the following steps: sweeps (or the cap in
+ * residual mode), tol (> 0: residual mode) and the residual check period. */
+tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t residual_every);
 
 /* Advance nsteps time steps (asynchronous). */
 tds_status tds_step(tds_scene *s, uint32_t nsteps);
@@ -166,8 +178,13 @@ tds_status tds_read_tool_force(tds_scene *s, float force[3], float torque[3]);
 tds_status tds_read_contacts(tds_scene *s, uint64_t *keys, float *lam, uint32_t *colour,
                              uint32_t cap, uint32_t *count);
 
-/* Statistics of the last step. Waits. */
+/* Statistics of the last step (phase times: summed since the previous call,
+ * which they reset). Waits. */
 tds_status tds_get_stats(tds_scene *s, tds_step_stats *out);
+
+/* Enable (1) or disable (0) per-phase timing with CUDA events recorded on the
+ * scene's stream around each phase of every step. */
+tds_status tds_set_timing(tds_scene *s, int32_t enable);
 
 void tds_destroy_scene(tds_scene *s);
 

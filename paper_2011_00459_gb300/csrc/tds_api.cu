@@ -10,14 +10,14 @@
 #include "tds_internal.cuh"
 
 // launchers (tds_contacts.cu, tds_colour.cu, tds_solve.cu)
-void tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st);
-void tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st);
-void tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
-                          int coop_threads, cudaStream_t st);
-void tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
+int tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st);
+int tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st);
+int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
+                         int coop_threads, cudaStream_t st);
+int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
                            uint32_t every, int apply_warm, int blocks, cudaStream_t st);
-void tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
+int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 const void *tds_pgs_kernel();
 const void *tds_colour_kernel();
@@ -92,7 +92,10 @@ struct tds_scene {
   int pgs_blocks = 1, colour_blocks = 1;
   uint64_t steps = 0;
   tds_status latched = TDS_OK;
-  std::vector<float> host_stage;
+  uint64_t launches = 0;
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;  // 6 per timed step
+  size_t ev_used = 0;
 };
 
 namespace {
@@ -225,6 +228,7 @@ size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) 
   }
   d.err = c.take<int32_t>(1);
   d.ctr = c.take<uint32_t>(CTR_COUNT);
+  d.acc = c.take<unsigned long long>(ACC_COUNT);
   d.fscal = c.take<float>(FS_COUNT);
   size_t nd = 2 * (size_t)pgs_blocks;
   if (nd < 6 * 128) nd = 6 * 128;
@@ -429,6 +433,7 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
        cudaMemcpyAsync(hf, desc->hf_heights, sizeof(float) * s->sz.hf_words, cudaMemcpyHostToDevice, s->st)) ||
       cudaMemsetAsync(s->d.err, 0, sizeof(int32_t), s->st) ||
       cudaMemsetAsync(s->d.ctr, 0, sizeof(uint32_t) * CTR_COUNT, s->st) ||
+      cudaMemsetAsync(s->d.acc, 0, sizeof(unsigned long long) * ACC_COUNT, s->st) ||
       cudaMemsetAsync(s->d.fscal, 0, sizeof(float) * FS_COUNT, s->st) ||
       cudaMemsetAsync(s->d.tool_out, 0, sizeof(float) * 6, s->st) ||
       cudaMemsetAsync(s->d.bucket_start, 0, sizeof(uint32_t) * (TDS_NBUCKETS + 1), s->st) ||
@@ -458,6 +463,15 @@ tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[
   return TDS_OK;
 }
 
+tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t residual_every) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (max_iters == 0 || !(tol >= 0.f)) return fail(TDS_ERR_INVALID_ARG, "max_iters >= 1 and tol >= 0 required");
+  s->desc.max_iters = max_iters;
+  s->desc.tol = tol;
+  s->desc.residual_every = residual_every ? residual_every : 1;
+  return TDS_OK;
+}
+
 tds_status tds_step(tds_scene *s, uint32_t nsteps) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
   tds_status ls = check_latched(s);
@@ -465,18 +479,35 @@ tds_status tds_step(tds_scene *s, uint32_t nsteps) {
   const tds_scene_desc &D = s->desc;
   for (uint32_t it = 0; it < nsteps; ++it) {
     DevPtrs &d = s->d;
-    tds_launch_broadphase(d, s->k, s->sz.ncells, s->st);
+    cudaEvent_t *E = nullptr;
+    if (s->timing) {
+      while (s->ev.size() < s->ev_used + 6) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        s->ev.push_back(e);
+      }
+      E = s->ev.data() + s->ev_used;
+      s->ev_used += 6;
+      CUDA_TRY(cudaEventRecord(E[0], s->st));
+    }
+    s->launches += tds_launch_broadphase(d, s->k, s->sz.ncells, s->st);
     std::swap(d.pos, d.pos2);
     std::swap(d.vel, d.vel2);
     std::swap(d.ang, d.ang2);
     std::swap(d.pid, d.pid2);
+    if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
     int use_prev = (D.warm_start == TDS_WARM_PREV) && s->have_prev;
-    tds_launch_narrowphase(d, s->k, use_prev, s->st);
-    tds_launch_predict(d, s->k, s->st);
-    tds_launch_colouring(d, s->sz.n, s->sz.cap, s->colour_blocks, 256, s->st);
+    s->launches += tds_launch_narrowphase(d, s->k, use_prev, s->st);
+    s->launches += tds_launch_predict(d, s->k, s->st);
+    if (E) CUDA_TRY(cudaEventRecord(E[2], s->st));
+    s->launches += tds_launch_colouring(d, s->sz.n, s->sz.cap, s->colour_blocks, 256, s->st);
+    if (E) CUDA_TRY(cudaEventRecord(E[3], s->st));
     CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev,
                             s->pgs_blocks, s->st));
-    tds_launch_finish(d, s->k, s->sz.cap, s->st);
+    s->launches += 1;
+    if (E) CUDA_TRY(cudaEventRecord(E[4], s->st));
+    s->launches += tds_launch_finish(d, s->k, s->sz.cap, s->st);
+    if (E) CUDA_TRY(cudaEventRecord(E[5], s->st));
     std::swap(d.prev_first[0], d.prev_first[1]);
     std::swap(d.prev_cnt[0], d.prev_cnt[1]);
     std::swap(d.prev_other[0], d.prev_other[1]);
@@ -528,10 +559,13 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   tds_status ls = check_latched(s);
   if (ls != TDS_OK) return ls;
   uint32_t ctr[CTR_COUNT];
+  unsigned long long acc[ACC_COUNT];
   float fs[FS_COUNT];
   std::vector<uint32_t> bs(TDS_NBUCKETS + 1);
   CUDA_TRY(cudaMemcpyAsync(ctr, s->d.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemcpyAsync(fs, s->d.fscal, sizeof(fs), cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(acc, s->d.acc, sizeof(acc), cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemsetAsync(s->d.acc, 0, sizeof(acc), s->st));
   CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bucket_start, sizeof(uint32_t) * bs.size(),
                            cudaMemcpyDeviceToHost, s->st));
   tds_status r = sync_and_check(s);
@@ -546,6 +580,26 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   out->iterations = ctr[CTR_ITERS];
   out->residual = fs[FS_RESID];
   out->steps = s->steps;
+  out->kernel_launches = s->launches;
+  out->sweep_contacts_pp = acc[ACC_SWEEP_PP];
+  out->sweep_contacts_static = acc[ACC_SWEEP_ST];
+  out->sum_contacts = acc[ACC_CONTACTS];
+  out->solved_steps = acc[ACC_STEPS];
+  out->timed_steps = (uint32_t)(s->ev_used / 6);
+  for (size_t b = 0; b + 6 <= s->ev_used; b += 6)
+    for (int q = 0; q < 5; ++q) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, s->ev[b + q], s->ev[b + q + 1]));
+      out->phase_ms[q] += ms;
+    }
+  s->ev_used = 0;
+  return TDS_OK;
+}
+
+tds_status tds_set_timing(tds_scene *s, int32_t enable) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  s->timing = enable != 0;
+  s->ev_used = 0;
   return TDS_OK;
 }
 
@@ -587,6 +641,7 @@ void tds_destroy_scene(tds_scene *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->owns && s->mem) cudaFree(s->mem);
   delete s;
 }

@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(DevPtrs d) {
 
 }  // namespace
 
-void tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
-                          int coop_threads, cudaStream_t st) {
+int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
+                         int coop_threads, cudaStream_t st) {
   unsigned gc = (cap + 255) / 256;
   if (gc > 152 * 16) gc = 152 * 16;
   if (gc == 0) gc = 1;
@@ -212,6 +212,7 @@ void tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_b
   tds_scan_exclusive(d.tile_hist, d.tile_off, TDS_NBUCKETS * d.ntiles, d.scan_tmp, st);
   k_bucket_starts<<<1, 256, 0, st>>>(d);
   k_bucket_scatter<<<d.ntiles, 256, 0, st>>>(d);
+  return 12;
 }
 
 const void *tds_colour_kernel() { return (const void *)k_colour_rounds; }

@@ -359,7 +359,7 @@ static inline unsigned grid_for(uint32_t n, unsigned threads, unsigned maxb = 15
   return b < maxb ? b : maxb;
 }
 
-void tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st) {
+int tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st) {
   cudaMemsetAsync(d.cell_count, 0, sizeof(uint32_t) * (ncells + 1), st);
   k_cells<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
   tds_scan_exclusive(d.cell_count, d.cell_start, ncells, d.scan_tmp, st);
@@ -367,12 +367,14 @@ void tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncell
   k_cell_scatter<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
   k_cell_sort<<<grid_for(ncells, 256), 256, 0, st>>>(d, ncells);
   k_reorder<<<grid_for(k.n, 256), 256, 0, st>>>(d, k.n);
+  return 8;
 }
 
 // After the reorder (pointers swapped by the caller): count, scan, write.
-void tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st) {
+int tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st) {
   k_count<<<grid_for(k.n, 128), 128, 0, st>>>(d, k);
   tds_scan_exclusive(d.cnt, d.cstart, k.n, d.scan_tmp, st);
   k_total<<<1, 1, 0, st>>>(d, k);
   k_write<<<grid_for(k.n, 128), 128, 0, st>>>(d, k, use_prev);
+  return 6;
 }

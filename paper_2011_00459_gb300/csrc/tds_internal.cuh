@@ -90,6 +90,7 @@ struct DevPtrs {
   // scalars and scratch
   int32_t *err;
   uint32_t *ctr;              // see CTR_* below
+  unsigned long long *acc;    // see ACC_* below (sums over steps, reset by the host)
   float *fscal;               // see FS_* below
   double *dpart;              // per-block partial sums
   uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
@@ -101,6 +102,9 @@ struct DevPtrs {
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_COUNT = 16 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
+// ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
+// static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.
+enum { ACC_SWEEP_PP = 0, ACC_SWEEP_ST = 1, ACC_CONTACTS = 2, ACC_STEPS = 3, ACC_COUNT = 8 };
 
 // ---------------------------------------------------------------------------
 // small helpers

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
       if (!grid_barrier(d.bar, d.err)) return;
     }
     ++it;
-    if (a.tol > 0.f && (it % a.every == 0 || it == a.max_iters)) {
+    if (it == a.max_iters || (a.tol > 0.f && it % a.every == 0)) {
       double num = 0.0, den = 0.0;
       for (uint32_t p = tid; p < nc; p += stride) {
         Row r = load_row(d, p);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
           td += __ldcg(d.dpart + 2 * b + 1);
         }
         resid = (float)(sqrt(tn) / fmax(sqrt(td), 1e-12));
-        s_stop = resid <= a.tol;
+        s_stop = a.tol > 0.f && resid <= a.tol;
       }
       __syncthreads();
       if (s_stop) break;
@@ -249,6 +249,12 @@ __global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d.ctr[CTR_ITERS] = it;
     d.fscal[FS_RESID] = resid;
+    uint32_t nst = 0;
+    for (uint32_t c = 0; c < ncol; ++c) nst += d.bucket_start[2 * c + 2] - d.bucket_start[2 * c + 1];
+    d.acc[ACC_SWEEP_PP] += (unsigned long long)it * (nc - nst);
+    d.acc[ACC_SWEEP_ST] += (unsigned long long)it * nst;
+    d.acc[ACC_CONTACTS] += nc;
+    d.acc[ACC_STEPS] += 1;
   }
 }
 
@@ -353,8 +359,9 @@ static inline unsigned grid_for(uint32_t n, unsigned threads, unsigned maxb = 15
   return b < maxb ? b : maxb;
 }
 
-void tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
+int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
   k_predict<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
+  return 1;
 }
 
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
@@ -366,12 +373,13 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
   return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(256), args, 0, st);
 }
 
-void tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st) {
+int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st) {
   k_writeback<<<grid_for(cap, 256), 256, 0, st>>>(d);
   k_prev_ranges<<<grid_for(k.n, 256), 256, 0, st>>>(d, k.n, cap);
   k_tool_partial<<<kToolBlocks, 256, 0, st>>>(d, k);
   k_tool_final<<<1, 32, 0, st>>>(d);
   k_integrate<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
+  return 5;
 }
 
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st) {

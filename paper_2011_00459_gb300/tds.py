@@ -25,7 +25,8 @@ STATIC_BIT = 0x80000000
 
 EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds_step",
             "tds_synchronize", "tds_read_particles", "tds_read_tool_force", "tds_read_contacts",
-            "tds_get_stats", "tds_destroy_scene", "tds_last_error"]
+            "tds_get_stats", "tds_set_timing", "tds_set_solver", "tds_destroy_scene",
+            "tds_last_error"]
 
 
 class TdsError(RuntimeError):
@@ -62,7 +63,12 @@ class StepStats(ctypes.Structure):
     _fields_ = [("n_contacts", ctypes.c_uint32), ("n_pp", ctypes.c_uint32),
                 ("n_static", ctypes.c_uint32), ("n_colours", ctypes.c_uint32),
                 ("iterations", ctypes.c_uint32), ("residual", ctypes.c_float),
-                ("steps", ctypes.c_uint64)]
+                ("steps", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
+                ("timed_steps", ctypes.c_uint32), ("phase_ms", ctypes.c_float * 5),
+                ("sweep_contacts_pp", ctypes.c_uint64), ("sweep_contacts_static", ctypes.c_uint64),
+                ("sum_contacts", ctypes.c_uint64), ("solved_steps", ctypes.c_uint64)]
+
+PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
 
 
 _lib = None
@@ -87,6 +93,8 @@ def lib() -> ctypes.CDLL:
         L.tds_read_contacts.argtypes = [vp, vp, vp, vp, ctypes.c_uint32,
                                         ctypes.POINTER(ctypes.c_uint32)]
         L.tds_get_stats.argtypes = [vp, ctypes.POINTER(StepStats)]
+        L.tds_set_timing.argtypes = [vp, ctypes.c_int32]
+        L.tds_set_solver.argtypes = [vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint32]
         L.tds_destroy_scene.argtypes = [vp]
         L.tds_destroy_scene.restype = None
         L.tds_last_error.restype = ctypes.c_char_p
@@ -249,7 +257,15 @@ class Scene:
     def stats(self) -> dict:
         st = StepStats()
         _check(lib().tds_get_stats(self.h, ctypes.byref(st)))
-        return {k: getattr(st, k) for k, _ in StepStats._fields_}
+        out = {k: getattr(st, k) for k, _ in StepStats._fields_ if k != "phase_ms"}
+        out["phase_ms"] = dict(zip(PHASES, st.phase_ms[:]))
+        return out
+
+    def set_solver(self, iters: int, tol: float = 0.0, residual_every: int = 10):
+        _check(lib().tds_set_solver(self.h, int(iters), float(tol), int(residual_every)))
+
+    def set_timing(self, enable: bool = True):
+        _check(lib().tds_set_timing(self.h, int(enable)))
 
     def close(self):
         if getattr(self, "h", None):
