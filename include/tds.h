@@ -188,6 +188,34 @@ tds_status tds_set_timing(tds_scene *s, int32_t enable);
 
 void tds_destroy_scene(tds_scene *s);
 
+/* ---- particle-pair contacts without any allocation -------------------------
+ * The paper has no counterpart to this call; it serves callers that cannot
+ * let a library allocate device memory: simulators stepping in a fixed-rate
+ * real-time loop, where cudaMalloc/cudaFree can synchronize the device and
+ * miss the frame, and applications whose device memory is owned by their own
+ * fixed-budget pool. It runs the particle-pair part of tds_step's contact
+ * search (sorted-cell broadphase and the same bit-exact FP32 predicate) on
+ * caller buffers and keeps its intermediate arrays in one file-scope device
+ * array of about 5.3 MB that every GPU loading the library holds until exit.
+ *
+ * x, y, z, radius: device pointers to n floats (particle i at index i);
+ * cohesive != 0 adds the cohesive band 0.025 (r_a + r_b) to the reach.
+ * keys: device pointer to cap uint64 slots; receives (a << 32) | b for every
+ * touching pair a < b, in no particular order (deterministic for equal
+ * inputs); count: device pointer to one uint32 that receives the number of
+ * pairs (if it exceeds cap, only cap keys were written). stream: a
+ * cudaStream_t or NULL. Asynchronous: results are ready when the stream is.
+ * n above TDS_NOALLOC_MAX_PARTICLES is rejected with TDS_ERR_CAPACITY.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. The first call
+ * on a device looks up the scratch array's device address (with that device
+ * current), so make it before any stream capture. All calls share the array:
+ * calls whose GPU work overlaps race, so keep them on one stream. */
+#define TDS_NOALLOC_MAX_PARTICLES 65536
+tds_status tds_find_pair_contacts_noalloc(const float *x, const float *y, const float *z,
+                                          const float *radius, uint32_t n, int32_t cohesive,
+                                          uint64_t *keys, uint32_t cap, uint32_t *count,
+                                          void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *tds_last_error(void);
 

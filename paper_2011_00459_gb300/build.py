@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtds.so")
 
-SOURCES = ["tds_api.cu", "tds_contacts.cu", "tds_colour.cu", "tds_solve.cu", "tds_scan.cu"]
+SOURCES = ["tds_api.cu", "tds_contacts.cu", "tds_colour.cu", "tds_solve.cu", "tds_scan.cu",
+           "tds_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -317,6 +317,9 @@ tds_status sync_and_check(tds_scene *s) {
 
 }  // namespace
 
+// Lets other translation units of the library report through tds_last_error.
+tds_status tds_set_error_message(tds_status s, const char *msg) { return fail(s, msg); }
+
 extern "C" {
 
 const char *tds_last_error(void) { return g_err.c_str(); }
