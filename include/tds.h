@@ -130,6 +130,7 @@ typedef struct {
   /* sums over the steps since the previous tds_get_stats (which resets them):
      sweeps x particle-pair contacts, sweeps x static contacts, contacts, steps */
   uint64_t sweep_contacts_pp, sweep_contacts_static, sum_contacts, solved_steps;
+  uint32_t colour_rounds;      /* rounds of the parallel greedy colouring, last step */
 } tds_step_stats;
 
 /* Bytes of device workspace a scene with this description needs. */

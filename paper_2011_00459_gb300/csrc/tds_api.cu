@@ -19,7 +19,7 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
                            uint32_t every, int apply_warm, int blocks, cudaStream_t st);
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
-const void *tds_pgs_kernel();
+int tds_pgs_setup(int *threads);
 const void *tds_colour_kernel();
 
 namespace {
@@ -187,9 +187,9 @@ Sizes plan(const tds_scene_desc *d) {
 
 size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) {
   const uint32_t n = s.n, cap = s.cap;
-  d.pos = c.take<float4>(n); d.vel = c.take<float4>(n); d.ang = c.take<float4>(n);
+  d.pos = c.take<float4>(n); d.pv = c.take<float4>(2 * (size_t)n);
   d.pid = c.take<uint32_t>(n);
-  d.pos2 = c.take<float4>(n); d.vel2 = c.take<float4>(n); d.ang2 = c.take<float4>(n);
+  d.pos2 = c.take<float4>(n); d.pv2 = c.take<float4>(2 * (size_t)n);
   d.pid2 = c.take<uint32_t>(n);
   d.cell_of = c.take<uint32_t>(n);
   d.cell_count = c.take<uint32_t>(s.ncells + 1);
@@ -205,20 +205,24 @@ size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) 
   d.c_sv = c.take<float4>(cap); d.c_sw = c.take<float4>(cap);
   d.c_la = c.take<float4>(cap); d.c_lb = c.take<float2>(cap);
   d.inc_cnt = c.take<uint32_t>(n + 1); d.inc_start = c.take<uint32_t>(n + 1);
-  d.inc_cursor = c.take<uint32_t>(n); d.inc_list = c.take<uint32_t>(2 * (size_t)cap);
+  d.inc_cursor = c.take<uint32_t>(n); d.inc_ent = c.take<uint2>(2 * (size_t)cap);
+  d.prio = c.take<unsigned long long>(cap);
   d.colour = c.take<uint8_t>(cap);
   d.wait = c.take<int32_t>(cap);
   d.frontier0 = c.take<uint32_t>(cap); d.frontier1 = c.take<uint32_t>(cap);
   d.ntiles = s.ntiles;
   d.tile_hist = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles);
   d.tile_off = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles + 1);
-  d.bucket_start = c.take<uint32_t>(TDS_NBUCKETS + 1);
-  d.order = c.take<uint32_t>(cap);
-  d.p_ab = c.take<uint2>(cap);
-  d.p_rn = c.take<float4>(cap); d.p_rq = c.take<float4>(cap);
-  d.p_rm = c.take<float2>(cap);
-  d.p_sv = c.take<float4>(cap); d.p_sw = c.take<float4>(cap);
-  d.p_la = c.take<float4>(cap); d.p_lb = c.take<float2>(cap);
+  d.bstart = c.take<uint32_t>(TDS_NBUCKETS + 1);
+  d.bend = c.take<uint32_t>(TDS_NBUCKETS);
+  d.bpad = c.take<uint32_t>(TDS_NBUCKETS);
+  const size_t pc = (size_t)cap + TDS_ORDER_PAD;  // colour order with padding
+  d.order = c.take<uint32_t>(pc);
+  d.p_ab = c.take<uint2>(pc);
+  d.p_rn = c.take<float4>(pc); d.p_rq = c.take<float4>(pc);
+  d.p_rm = c.take<float2>(pc);
+  d.p_sv = c.take<float4>(pc); d.p_sw = c.take<float4>(pc);
+  d.p_la = c.take<float4>(pc); d.p_lb = c.take<float2>(pc);
   for (int b = 0; b < 2; ++b) {
     d.prev_first[b] = c.take<uint32_t>(n);
     d.prev_cnt[b] = c.take<uint32_t>(n);
@@ -355,15 +359,15 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
   int dev = 0, sms = 0, occ_pgs = 0, occ_col = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pgs, tds_pgs_kernel(), 256, 0);
+  int pgs_threads = 0;
+  if (ce == cudaSuccess) occ_pgs = tds_pgs_setup(&pgs_threads);
   if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_col, tds_colour_kernel(), 256, 0);
   if (ce != cudaSuccess || occ_pgs < 1 || occ_col < 1) {
     delete s;
     return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
   }
-  int max_pgs = sms * (occ_pgs < 4 ? occ_pgs : 4);
-  s->pgs_blocks = pgs_blocks_for(desc->n, max_pgs);
-  s->colour_blocks = sms * (occ_col < 2 ? occ_col : 2);
+  s->pgs_blocks = pgs_blocks_for(desc->n, sms);  // one co-resident CTA per SM at most
+  s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
   float *hf = nullptr;
   Carver probe{nullptr};
   DevPtrs tmp{};
@@ -409,7 +413,7 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
   compose_boxes(s);
   // upload particle state: (x, r), (v, 1/m), (w, 1/I), ids
   const uint32_t n = desc->n;
-  std::vector<float4> P(n), V(n), W(n);
+  std::vector<float4> P(n), PV(2 * (size_t)n);
   std::vector<uint32_t> ids(n);
   const double pi = 3.14159265358979323846;
   for (uint32_t i = 0; i < n; ++i) {
@@ -417,10 +421,10 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
     double m = desc->density * 4.0 / 3.0 * pi * r * r * r;
     double I = 0.4 * m * r * r;
     P[i] = make_float4(desc->x[i], desc->y[i], desc->z[i], desc->radius[i]);
-    V[i] = make_float4(desc->vx ? desc->vx[i] : 0.f, desc->vy ? desc->vy[i] : 0.f,
-                       desc->vz ? desc->vz[i] : 0.f, (float)(1.0 / m));
-    W[i] = make_float4(desc->wx ? desc->wx[i] : 0.f, desc->wy ? desc->wy[i] : 0.f,
-                       desc->wz ? desc->wz[i] : 0.f, (float)(1.0 / I));
+    PV[2 * i] = make_float4(desc->vx ? desc->vx[i] : 0.f, desc->vy ? desc->vy[i] : 0.f,
+                            desc->vz ? desc->vz[i] : 0.f, (float)(1.0 / m));
+    PV[2 * i + 1] = make_float4(desc->wx ? desc->wx[i] : 0.f, desc->wy ? desc->wy[i] : 0.f,
+                                desc->wz ? desc->wz[i] : 0.f, (float)(1.0 / I));
     ids[i] = i;
   }
   auto cleanup_fail = [&](const std::string &msg) {
@@ -429,8 +433,7 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
     return fail(TDS_ERR_CUDA, msg);
   };
   if (cudaMemcpyAsync(s->d.pos, P.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
-      cudaMemcpyAsync(s->d.vel, V.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
-      cudaMemcpyAsync(s->d.ang, W.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
+      cudaMemcpyAsync(s->d.pv, PV.data(), sizeof(float4) * 2 * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.pid, ids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
       (desc->hf_nx > 0 &&
        cudaMemcpyAsync(hf, desc->hf_heights, sizeof(float) * s->sz.hf_words, cudaMemcpyHostToDevice, s->st)) ||
@@ -439,7 +442,8 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
       cudaMemsetAsync(s->d.acc, 0, sizeof(unsigned long long) * ACC_COUNT, s->st) ||
       cudaMemsetAsync(s->d.fscal, 0, sizeof(float) * FS_COUNT, s->st) ||
       cudaMemsetAsync(s->d.tool_out, 0, sizeof(float) * 6, s->st) ||
-      cudaMemsetAsync(s->d.bucket_start, 0, sizeof(uint32_t) * (TDS_NBUCKETS + 1), s->st) ||
+      cudaMemsetAsync(s->d.bstart, 0, sizeof(uint32_t) * (TDS_NBUCKETS + 1), s->st) ||
+      cudaMemsetAsync(s->d.bend, 0, sizeof(uint32_t) * TDS_NBUCKETS, s->st) ||
       cudaStreamSynchronize(s->st)) {
     cudaGetLastError();
     return cleanup_fail("uploading the scene failed");
@@ -495,8 +499,7 @@ tds_status tds_step(tds_scene *s, uint32_t nsteps) {
     }
     s->launches += tds_launch_broadphase(d, s->k, s->sz.ncells, s->st);
     std::swap(d.pos, d.pos2);
-    std::swap(d.vel, d.vel2);
-    std::swap(d.ang, d.ang2);
+    std::swap(d.pv, d.pv2);
     std::swap(d.pid, d.pid2);
     if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
     int use_prev = (D.warm_start == TDS_WARM_PREV) && s->have_prev;
@@ -564,22 +567,25 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   uint32_t ctr[CTR_COUNT];
   unsigned long long acc[ACC_COUNT];
   float fs[FS_COUNT];
-  std::vector<uint32_t> bs(TDS_NBUCKETS + 1);
+  std::vector<uint32_t> bs(TDS_NBUCKETS + 1), be(TDS_NBUCKETS);
   CUDA_TRY(cudaMemcpyAsync(ctr, s->d.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemcpyAsync(fs, s->d.fscal, sizeof(fs), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemcpyAsync(acc, s->d.acc, sizeof(acc), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemsetAsync(s->d.acc, 0, sizeof(acc), s->st));
-  CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bucket_start, sizeof(uint32_t) * bs.size(),
+  CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bstart, sizeof(uint32_t) * bs.size(),
+                           cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(be.data(), s->d.bend, sizeof(uint32_t) * be.size(),
                            cudaMemcpyDeviceToHost, s->st));
   tds_status r = sync_and_check(s);
   if (r != TDS_OK) return r;
   std::memset(out, 0, sizeof(*out));
   out->n_contacts = ctr[CTR_NC];
   uint32_t nst = 0;
-  for (int c = 0; c < TDS_MAX_COLOURS; ++c) nst += bs[2 * c + 2] - bs[2 * c + 1];
+  for (int c = 0; c < TDS_MAX_COLOURS; ++c) nst += be[2 * c + 1] - bs[2 * c + 1];
   out->n_static = nst;
   out->n_pp = ctr[CTR_NC] - nst;
   out->n_colours = ctr[CTR_NCOL];
+  out->colour_rounds = ctr[CTR_ROUNDS];
   out->iterations = ctr[CTR_ITERS];
   out->residual = fs[FS_RESID];
   out->steps = s->steps;

@@ -16,37 +16,56 @@ namespace {
 
 __device__ __forceinline__ bool is_dyn(uint32_t b) { return (b & TDS_STATIC) == 0u; }
 
+// Incidence counts per particle and each contact's priority (computed once).
 __global__ void k_inc_count(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     uint2 ab = d.c_ab[c];
+    d.prio[c] = priority(d.c_key[c]);
     atomicAdd(d.inc_cnt + ab.x, 1u);
     if (is_dyn(ab.y)) atomicAdd(d.inc_cnt + ab.y, 1u);
   }
 }
 
+// Incidence entries carry the contact id and the high word of its priority,
+// so walking a neighbourhood needs no dependent loads to compare priorities.
 __global__ void k_inc_fill(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     uint2 ab = d.c_ab[c];
-    d.inc_list[atomicAdd(d.inc_cursor + ab.x, 1u)] = c;
-    if (is_dyn(ab.y)) d.inc_list[atomicAdd(d.inc_cursor + ab.y, 1u)] = c;
+    uint32_t hi = (uint32_t)(d.prio[c] >> 32);
+    d.inc_ent[atomicAdd(d.inc_cursor + ab.x, 1u)] = make_uint2(c, hi);
+    if (is_dyn(ab.y)) d.inc_ent[atomicAdd(d.inc_cursor + ab.y, 1u)] = make_uint2(c, hi);
   }
 }
+
+// Is neighbour entry e of higher priority than contact c (priority pc)?
+// The high words decide unless they tie; then the full priorities do.
+__device__ __forceinline__ bool higher(const DevPtrs &d, uint2 e, unsigned long long pc) {
+  uint32_t hc = (uint32_t)(pc >> 32);
+  if (e.y != hc) return e.y > hc;
+  return d.prio[e.x] > pc;
+}
+
+constexpr int kBatch = 8;
 
 // wait[c] = number of neighbours of higher priority; sources start round 0.
 __global__ void k_colour_init(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     uint2 ab = d.c_ab[c];
-    unsigned long long pc = priority(d.c_key[c]);
+    unsigned long long pc = d.prio[c];
     int32_t w = 0;
     uint32_t ends[2] = {ab.x, ab.y};
-    for (int e = 0; e < 2; ++e) {
-      if (!is_dyn(ends[e])) continue;
-      for (uint32_t m = d.inc_start[ends[e]]; m < d.inc_start[ends[e] + 1]; ++m) {
-        uint32_t o = d.inc_list[m];
-        if (o != c && priority(d.c_key[o]) > pc) ++w;
+    for (int k = 0; k < 2; ++k) {
+      if (!is_dyn(ends[k])) continue;
+      const uint32_t s = d.inc_start[ends[k]], e = d.inc_start[ends[k] + 1];
+      for (uint32_t m0 = s; m0 < e; m0 += kBatch) {
+        uint2 ent[kBatch];
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
+#pragma unroll
+        for (int q = 0; q < kBatch; ++q) w += (ent[q].x != c && higher(d, ent[q], pc)) ? 1 : 0;
       }
     }
     d.wait[c] = w;
@@ -58,14 +77,17 @@ __global__ void k_colour_init(DevPtrs d) {
   }
 }
 
-// Persistent, co-resident launch: one round per grid barrier.
+// Persistent, co-resident launch: one round per grid barrier. A round colours
+// every contact whose higher-priority neighbours are all coloured, then
+// releases its lower-priority neighbours into the next round's frontier.
 __global__ void k_colour_rounds(DevPtrs d) {
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t nc = d.ctr[CTR_NC];
   __shared__ uint32_t s_maxcol;
   if (threadIdx.x == 0) s_maxcol = 0;
   __syncthreads();
-  for (uint32_t round = 0;; ++round) {
+  uint32_t round = 0, gen = 0;
+  for (;; ++round) {
     uint32_t *cur = (round & 1) ? d.frontier1 : d.frontier0;
     uint32_t *nxt = (round & 1) ? d.frontier0 : d.frontier1;
     volatile uint32_t *fc = d.ctr + CTR_FCOUNT;
@@ -73,19 +95,28 @@ __global__ void k_colour_rounds(DevPtrs d) {
     uint32_t *push = d.ctr + CTR_FCOUNT + (round + 1) % 3;
     if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr[CTR_FCOUNT + (round + 2) % 3] = 0u;
     for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < ncur; idx += stride) {
-      uint32_t c = __ldcg(cur + idx);
-      uint2 ab = d.c_ab[c];
-      unsigned long long pc = priority(d.c_key[c]);
+      const uint32_t c = __ldcg(cur + idx);
+      const uint2 ab = d.c_ab[c];
+      const unsigned long long pc = d.prio[c];
       unsigned long long used0 = 0ull, used1 = 0ull;
-      uint32_t ends[2] = {ab.x, ab.y};
-      for (int e = 0; e < 2; ++e) {
-        if (!is_dyn(ends[e])) continue;
-        for (uint32_t m = d.inc_start[ends[e]]; m < d.inc_start[ends[e] + 1]; ++m) {
-          uint32_t o = d.inc_list[m];
-          if (o == c || priority(d.c_key[o]) < pc) continue;
-          uint32_t col = __ldcg(d.colour + o);
-          if (col < 64) used0 |= 1ull << col;
-          else if (col < 128) used1 |= 1ull << (col - 64);
+      const uint32_t ends[2] = {ab.x, ab.y};
+      // colours of the higher-priority neighbours (all coloured already)
+      for (int k = 0; k < 2; ++k) {
+        if (!is_dyn(ends[k])) continue;
+        const uint32_t s = d.inc_start[ends[k]], e = d.inc_start[ends[k] + 1];
+        for (uint32_t m0 = s; m0 < e; m0 += kBatch) {
+          uint2 ent[kBatch];
+          uint32_t col[kBatch];
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q)
+            col[q] = (ent[q].x != c && higher(d, ent[q], pc)) ? (uint32_t)__ldcg(d.colour + ent[q].x) : 0xFFu;
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q) {
+            if (col[q] < 64) used0 |= 1ull << col[q];
+            else if (col[q] < 128) used1 |= 1ull << (col[q] - 64);
+          }
         }
       }
       uint32_t col;
@@ -95,23 +126,33 @@ __global__ void k_colour_rounds(DevPtrs d) {
       __stcg(d.colour + c, (uint8_t)col);
       atomicMax(&s_maxcol, col + 1);
       __threadfence();
-      for (int e = 0; e < 2; ++e) {
-        if (!is_dyn(ends[e])) continue;
-        for (uint32_t m = d.inc_start[ends[e]]; m < d.inc_start[ends[e] + 1]; ++m) {
-          uint32_t o = d.inc_list[m];
-          if (o == c || priority(d.c_key[o]) > pc) continue;
-          if (atomicSub(d.wait + o, 1) == 1) {
-            uint32_t q = atomicAdd(push, 1u);
-            if (q < nc) nxt[q] = o;
-          }
+      // release the lower-priority neighbours
+      for (int k = 0; k < 2; ++k) {
+        if (!is_dyn(ends[k])) continue;
+        const uint32_t s = d.inc_start[ends[k]], e = d.inc_start[ends[k] + 1];
+        for (uint32_t m0 = s; m0 < e; m0 += kBatch) {
+          uint2 ent[kBatch];
+          int32_t old[kBatch];
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q)
+            old[q] = (ent[q].x != c && !higher(d, ent[q], pc)) ? atomicSub(d.wait + ent[q].x, 1) : 0;
+#pragma unroll
+          for (int q = 0; q < kBatch; ++q)
+            if (old[q] == 1) {
+              uint32_t slot = atomicAdd(push, 1u);
+              if (slot < nc) nxt[slot] = ent[q].x;
+            }
         }
       }
     }
-    if (!grid_barrier(d.bar, d.err)) return;
+    if (!grid_barrier(d.bar, d.err, gen)) return;
     if (fc[(round + 1) % 3] == 0u || round > nc) break;
   }
   __syncthreads();
   if (threadIdx.x == 0) atomicMax(d.ctr + CTR_NCOL, s_maxcol);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.ctr[CTR_ROUNDS] = round + 1;
 }
 
 // ---- stable counting sort of contacts by bucket = 2 colour + static? ------
@@ -141,9 +182,23 @@ __global__ void k_bucket_hist(DevPtrs d) {
     d.tile_hist[b * d.ntiles + blockIdx.x] = hist[b];
 }
 
+// Bucket ranges in the padded colour order: every bucket starts at a multiple
+// of 4 contacts (16-byte aligned rows for bulk copies); padding slots carry
+// order == 0xFFFFFFFF and are never solved.
 __global__ void k_bucket_starts(DevPtrs d) {
-  for (uint32_t b = threadIdx.x; b <= TDS_NBUCKETS; b += blockDim.x)
-    d.bucket_start[b] = b < TDS_NBUCKETS ? d.tile_off[b * d.ntiles] : d.ctr[CTR_NC];
+  if (threadIdx.x != 0) return;
+  uint32_t run = 0;
+  for (uint32_t b = 0; b < TDS_NBUCKETS; ++b) {
+    uint32_t u0 = d.tile_off[b * d.ntiles];
+    uint32_t u1 = b + 1 < TDS_NBUCKETS ? d.tile_off[(b + 1) * d.ntiles] : d.ctr[CTR_NC];
+    uint32_t cnt = u1 - u0;
+    d.bstart[b] = run;
+    d.bend[b] = run + cnt;
+    d.bpad[b] = run - u0;
+    run += (cnt + 3u) & ~3u;
+  }
+  d.bstart[TDS_NBUCKETS] = run;
+  d.ctr[CTR_PADDED] = run;
 }
 
 // Scatter every contact's rows to its colour-order position: tile offset of
@@ -174,7 +229,7 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(DevPtrs d) {
     }
     __syncthreads();
     if (live) {
-      uint32_t p = wcnt[warp][bk] + rank_in_warp;
+      uint32_t p = wcnt[warp][bk] + rank_in_warp + d.bpad[bk];
       d.order[p] = c;
       d.p_ab[p] = d.c_ab[c];
       d.p_rn[p] = d.c_rn[c];
@@ -210,7 +265,9 @@ int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_bl
                               args, 0, st);
   k_bucket_hist<<<d.ntiles, 256, 0, st>>>(d);
   tds_scan_exclusive(d.tile_hist, d.tile_off, TDS_NBUCKETS * d.ntiles, d.scan_tmp, st);
-  k_bucket_starts<<<1, 256, 0, st>>>(d);
+  k_bucket_starts<<<1, 32, 0, st>>>(d);
+  cudaMemsetAsync(d.order, 0xFF, sizeof(uint32_t) * ((size_t)cap + TDS_ORDER_PAD), st);
+  cudaMemsetAsync(d.p_ab, 0xFF, sizeof(uint2) * ((size_t)cap + TDS_ORDER_PAD), st);  // padding sentinel
   k_bucket_scatter<<<d.ntiles, 256, 0, st>>>(d);
   return 12;
 }

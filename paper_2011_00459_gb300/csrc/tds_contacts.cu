@@ -148,8 +148,7 @@ __global__ void k_reorder(DevPtrs d, uint32_t n) {
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     uint32_t i = d.perm[j];
     d.pos2[j] = d.pos[i];
-    d.vel2[j] = d.vel[i];
-    d.ang2[j] = d.ang[i];
+    reinterpret_cast<double4 *>(d.pv2)[j] = reinterpret_cast<const double4 *>(d.pv)[i];
     d.pid2[j] = d.pid[i];
   }
 }
@@ -216,7 +215,7 @@ struct Writer {
   const DevPtrs &d;
   const StepConsts &k;
   uint32_t i, me, next;
-  float4 P, Va, Wa;
+  float4 P, Va;
   int use_prev;
   uint32_t pf, pc;
 
@@ -285,7 +284,7 @@ struct Writer {
     float delta = P.w + Q.w - dist;
     float rs = P.w + Q.w;
     float dstar = 2.0f * P.w * Q.w / rs;
-    float4 Vb = d.vel[j];
+    float4 Vb = d.pv[2 * j];
     float3 z3 = make_float3(0.f, 0.f, 0.f);
     emit(j, pj, n, delta, Q.w, dstar, k.estar_pair, dstar, 1e-5f * rs, false, false, f3(Vb), z3, z3);
   }
@@ -339,7 +338,7 @@ struct Writer {
 
 __global__ void k_write(DevPtrs d, StepConsts k, int use_prev) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
-    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.vel[i], d.ang[i], use_prev, 0u, 0u};
+    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.pv[2 * i], use_prev, 0u, 0u};
     if (use_prev) {
       w.pf = d.prev_first[0][w.me];
       w.pc = d.prev_cnt[0][w.me];

@@ -11,6 +11,7 @@
 #define TDS_MAX_COLOURS 128
 #define TDS_NBUCKETS (2 * TDS_MAX_COLOURS)  // (colour, static?) buckets
 #define TDS_TILE 2048                       // contacts per bucketing tile
+#define TDS_ORDER_PAD (4 * TDS_NBUCKETS + 16) // padding slots of the colour order
 #define TDS_BARRIER_NS 2000000000ull        // 2 s limit on any grid-barrier wait
 
 // Error codes latched on the device (the tds_status values).
@@ -54,9 +55,10 @@ struct StepConsts {
 // Device pointers of one scene (passed by value).
 struct DevPtrs {
   // particles, slot order (re-sorted by cell every step)
-  float4 *pos, *vel, *ang;    // (x,y,z,r), (v, 1/m), (w, 1/I)
+  float4 *pos;                // (x, y, z, r)
+  float4 *pv;                 // 32-byte state record per particle: [2i] (v, 1/m), [2i+1] (w, 1/I)
   uint32_t *pid;
-  float4 *pos2, *vel2, *ang2; // reorder targets
+  float4 *pos2, *pv2;         // reorder targets
   uint32_t *pid2;
   // grid
   uint32_t *cell_of, *cell_count, *cell_start, *cell_cursor, *perm;
@@ -70,12 +72,15 @@ struct DevPtrs {
   float4 *c_la;               // initial impulses (n, t1, t2, r.x)
   float2 *c_lb;               // (r.y, r.z)
   // colouring
-  uint32_t *inc_cnt, *inc_start, *inc_cursor, *inc_list;
+  uint32_t *inc_cnt, *inc_start, *inc_cursor;
+  uint2 *inc_ent;             // (contact id, high word of its priority) per incidence
+  unsigned long long *prio;   // colouring priority per contact
   uint8_t *colour;
   int32_t *wait;
   uint32_t *frontier0, *frontier1;
   // bucketing into colour order
-  uint32_t *tile_hist, *tile_off, *bucket_start, *order;
+  uint32_t *tile_hist, *tile_off, *order;
+  uint32_t *bstart, *bend, *bpad;  // padded colour-order range of each bucket
   uint32_t ntiles;
   // colour order (what the solver streams)
   uint2 *p_ab;
@@ -100,7 +105,7 @@ struct DevPtrs {
 };
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
-       CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_COUNT = 16 };
+       CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_COUNT = 16 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
 // ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
 // static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.
@@ -110,6 +115,19 @@ enum { ACC_SWEEP_PP = 0, ACC_SWEEP_ST = 1, ACC_CONTACTS = 2, ACC_STEPS = 3, ACC_
 // small helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+
+// One 256-bit access (a single 32-byte sector) for a particle's state
+// record, bypassing L1 (other SMs update it between colours).
+__device__ __forceinline__ void ld_state(const float4 *rec, float4 &v, float4 &w) {
+  asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w), "=f"(w.x), "=f"(w.y), "=f"(w.z), "=f"(w.w)
+               : "l"(rec));
+}
+__device__ __forceinline__ void st_state(float4 *rec, float4 v, float4 w) {
+  asm volatile("st.global.cg.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(rec), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w)
+               : "memory");
+}
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
@@ -124,7 +142,7 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 // under the choice of basis, since its effective mass is isotropic.
 __device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
   float sgn = copysignf(1.0f, n.z);
-  float a = -1.0f / (sgn + n.z);
+  float a = -__frcp_rn(sgn + n.z);
   float b = n.x * n.y * a;
   t1 = make_float3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
   t2 = make_float3(b, sgn + n.y * n.y * a, -n.y);
@@ -149,42 +167,42 @@ __device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
   atomicCAS(err, 0, code);
 }
 
-// Grid-wide barrier for cooperative (co-resident) launches: arrival counter
-// plus generation word, bounded wait. Returns false (and latches
-// DEV_ERR_BARRIER) if the wait ran past TDS_BARRIER_NS or another block
-// already failed; the caller must then return.
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err) {
+// Grid-wide barrier for cooperative (co-resident) launches over one arrival
+// counter that is zeroed before each launch. gen counts the barriers this
+// block has passed (the same for every block): thread 0 adds 1 with release
+// semantics (publishing the block's writes, ordered by the preceding
+// __syncthreads) without waiting for a reply, then polls with acquire loads
+// until the counter reaches (gen + 1) x gridDim.x. The wait is bounded: past
+// TDS_BARRIER_NS, or when another block latched an error, it returns false
+// (latching DEV_ERR_BARRIER on a timeout) and the caller must return.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err, uint32_t &gen) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile uint32_t *vgen = bar + 1;
-    uint32_t gen = *vgen;
-    __threadfence();
-    uint32_t arrived = atomicAdd(bar, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    const uint32_t target = (gen + 1u) * gridDim.x;
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (*vgen == gen) {
-        if (((++spins) & 63u) == 0) {
-          if (*(volatile int32_t *)err != 0) { ok = 0; break; }
-          if (global_ns() - t0 > TDS_BARRIER_NS) {
-            latch_error(err, DEV_ERR_BARRIER);
-            ok = 0;
-            break;
-          }
+    unsigned long long t0 = 0;
+    for (unsigned spins = 0;; ++spins) {
+      uint32_t cur;
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+      if ((int32_t)(cur - target) >= 0) break;
+      if ((spins & 31u) == 31u) {
+        if (*(volatile int32_t *)err != 0) { ok = 0; break; }
+        unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > TDS_BARRIER_NS) {
+          latch_error(err, DEV_ERR_BARRIER);
+          ok = 0;
+          break;
         }
       }
     }
-    __threadfence();
     if (*(volatile int32_t *)err != 0) ok = 0;
     s_ok = ok;
   }
   __syncthreads();
+  ++gen;
   return s_ok != 0;
 }
 

@@ -21,11 +21,11 @@ __device__ __forceinline__ bool is_dyn(uint32_t b) { return (b & TDS_STATIC) == 
 
 __global__ void k_predict(DevPtrs d, StepConsts k) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
-    float4 v = d.vel[i];
+    float4 v = d.pv[2 * i];
     v.x += k.dt * k.g[0];
     v.y += k.dt * k.g[1];
     v.z += k.dt * k.g[2];
-    d.vel[i] = v;
+    d.pv[2 * i] = v;
   }
 }
 
@@ -35,12 +35,13 @@ struct Side {
 };
 
 __device__ __forceinline__ Side load_side(const DevPtrs &d, uint32_t s) {
-  float4 v = __ldcg(d.vel + s), w = __ldcg(d.ang + s);
+  float4 v, w;
+  ld_state(d.pv + 2 * (size_t)s, v, w);
   return Side{f3(v), f3(w), v.w, w.w};
 }
 __device__ __forceinline__ void store_side(const DevPtrs &d, uint32_t s, const Side &x) {
-  __stcg(d.vel + s, make_float4(x.v.x, x.v.y, x.v.z, x.im));
-  __stcg(d.ang + s, make_float4(x.w.x, x.w.y, x.w.z, x.iI));
+  st_state(d.pv + 2 * (size_t)s, make_float4(x.v.x, x.v.y, x.v.z, x.im),
+           make_float4(x.w.x, x.w.y, x.w.z, x.iI));
 }
 
 struct Row {
@@ -65,79 +66,98 @@ __device__ __forceinline__ Row load_row(const DevPtrs &d, uint32_t p) {
   return r;
 }
 
+// Projections on the Coulomb disk / rolling ball of radius bound (a zero
+// bound forces zero).
 __device__ __forceinline__ void disk(float &a, float &b, float bound) {
-  float m = sqrtf(a * a + b * b);
-  if (m > bound) { float s = bound > 0.f ? bound / m : 0.f; a *= s; b *= s; }
-}
-__device__ __forceinline__ void ball(float3 &a, float bound) {
-  float m = sqrtf(dot(a, a));
-  if (m > bound) a = (bound > 0.f ? bound / m : 0.f) * a;
-}
-
-// v += M^-1 G^T (dn, dt(world), dr) on both sides.
-__device__ __forceinline__ void apply(const Row &r, Side &A, Side &B, float dn, float3 dt, float3 dr) {
-  float3 P = dn * r.n + dt;
-  A.v = A.v - A.im * P;
-  A.w = A.w - A.iI * (cross(r.la * r.n, dt) + dr);
-  if (r.dyn) {
-    B.v = B.v + B.im * P;
-    B.w = B.w + B.iI * (cross((-r.lb) * r.n, dt) + dr);
+  const float m2 = a * a + b * b;
+  if (m2 > bound * bound) {
+    const float s = bound > 0.f ? bound * rsqrtf(m2) : 0.f;
+    a *= s;
+    b *= s;
   }
 }
+__device__ __forceinline__ void ball(float3 &a, float bound) {
+  const float m2 = dot(a, a);
+  if (m2 > bound * bound) a = (bound > 0.f ? bound * rsqrtf(m2) : 0.f) * a;
+}
 
+// v += M^-1 G^T dLambda for each row group. A static side has zero inverse
+// mass and inertia, so its (discarded) update is a no-op.
+__device__ __forceinline__ void apply_normal(const Row &r, Side &A, Side &B, float dn) {
+  const float3 P = dn * r.n;
+  A.v = A.v - A.im * P;
+  B.v = B.v + B.im * P;
+}
+__device__ __forceinline__ void apply_tangent(const Row &r, Side &A, Side &B, float3 dt) {
+  const float3 c = cross(r.n, dt);  // torque arms: +la n on a, -lb n on b
+  A.v = A.v - A.im * dt;
+  A.w = A.w - (A.iI * r.la) * c;
+  B.v = B.v + B.im * dt;
+  B.w = B.w - (B.iI * r.lb) * c;
+}
+__device__ __forceinline__ void apply_rolling(Side &A, Side &B, float3 dr) {
+  A.w = A.w - A.iI * dr;
+  B.w = B.w + B.iI * dr;
+}
+// v += M^-1 G^T (dn, dt(world), dr) on both sides.
+__device__ __forceinline__ void apply(const Row &r, Side &A, Side &B, float dn, float3 dt, float3 dr) {
+  apply_normal(r, A, B, dn);
+  apply_tangent(r, A, B, dt);
+  apply_rolling(A, B, dr);
+}
+
+// Relative velocity of the contact points:
+// (v_b + w_b x (-lb n)) - (v_a + w_a x (la n)) = (v_b - v_a) - (lb w_b + la w_a) x n
 __device__ __forceinline__ float3 slip(const Row &r, const Side &A, const Side &B) {
-  return (B.v + cross(B.w, (-r.lb) * r.n)) - (A.v + cross(A.w, r.la * r.n));
+  return (B.v - A.v) - cross(r.lb * B.w + r.la * A.w, r.n);
 }
 
 // One projected Gauss-Seidel update of one contact.
 __device__ __forceinline__ void pgs_update(const Row &r, Side &A, Side &B, float4 &L0, float2 &L1,
                                            float sig_t, float sig_r) {
-  const float3 z3 = make_float3(0.f, 0.f, 0.f);
   // normal row
-  float Dn = A.im + B.im + r.Sn;
-  float res = dot(r.n, B.v - A.v) + r.Sn * L0.x - r.qn;
-  float ln = fmaxf(L0.x - res / Dn, -r.fc);
-  float dln = ln - L0.x;
+  const float iDn = __frcp_rn(A.im + B.im + r.Sn);
+  const float res = dot(r.n, B.v - A.v) + r.Sn * L0.x - r.qn;
+  const float ln = fmaxf(L0.x - res * iDn, -r.fc);
+  apply_normal(r, A, B, ln - L0.x);
   L0.x = ln;
-  apply(r, A, B, dln, z3, z3);
   // tangent rows (Coulomb disk)
   float3 t1, t2;
   onb(r.n, t1, t2);
-  float Dt = A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t;
-  float3 u = slip(r, A, B);
-  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) / Dt;
-  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) / Dt;
+  const float iDt = __frcp_rn(A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t);
+  const float3 u = slip(r, A, B);
+  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) * iDt;
+  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) * iDt;
   disk(y1, y2, r.mu * fabsf(ln));
-  float3 dt = (y1 - L0.y) * t1 + (y2 - L0.z) * t2;
-  L0.y = y1; L0.z = y2;
-  apply(r, A, B, 0.f, dt, z3);
+  apply_tangent(r, A, B, (y1 - L0.y) * t1 + (y2 - L0.z) * t2);
+  L0.y = y1;
+  L0.z = y2;
   // rolling rows (ball)
-  float Dr = A.iI + B.iI + sig_r;
-  float3 lr = make_float3(L0.w, L1.x, L1.y);
-  float3 y = lr - (1.0f / Dr) * ((B.w - A.w) + sig_r * lr);
+  const float iDr = __frcp_rn(A.iI + B.iI + sig_r);
+  const float3 lr = make_float3(L0.w, L1.x, L1.y);
+  float3 y = lr - iDr * ((B.w - A.w) + sig_r * lr);
   ball(y, r.rmu * fabsf(ln));
-  float3 dr = y - lr;
-  L0.w = y.x; L1.x = y.y; L1.y = y.z;
-  apply(r, A, B, 0.f, z3, dr);
+  apply_rolling(A, B, y - lr);
+  L0.w = y.x;
+  L1.x = y.y;
+  L1.y = y.z;
 }
 
 // Contribution of one contact to the natural-map residual (Jacobi pass).
 __device__ __forceinline__ void resid_terms(const Row &r, const Side &A, const Side &B, float4 L0,
                                             float2 L1, float sig_t, float sig_r, double &num,
                                             double &den) {
-  float Dn = A.im + B.im + r.Sn;
   float wn = dot(r.n, B.v - A.v) + r.Sn * L0.x - r.qn;
-  float pn = fmaxf(L0.x - wn / Dn, -r.fc);
+  float pn = fmaxf(L0.x - wn * __frcp_rn(A.im + B.im + r.Sn), -r.fc);
   float3 t1, t2;
   onb(r.n, t1, t2);
-  float Dt = A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t;
+  float iDt = __frcp_rn(A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t);
   float3 u = slip(r, A, B);
-  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) / Dt;
-  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) / Dt;
+  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) * iDt;
+  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) * iDt;
   disk(y1, y2, r.mu * fabsf(L0.x));
-  float Dr = A.iI + B.iI + sig_r;
   float3 lr = make_float3(L0.w, L1.x, L1.y);
-  float3 y = lr - (1.0f / Dr) * ((B.w - A.w) + sig_r * lr);
+  float3 y = lr - __frcp_rn(A.iI + B.iI + sig_r) * ((B.w - A.w) + sig_r * lr);
   ball(y, r.rmu * fabsf(L0.x));
   float e0 = L0.x - pn, e1 = L0.y - y1, e2 = L0.z - y2;
   float3 e3 = lr - y;
@@ -170,69 +190,257 @@ struct SolveArgs {
   int apply_warm;
 };
 
-__global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
-  __shared__ double sh[8];
-  __shared__ int s_stop;
-  const uint32_t ncol = d.ctr[CTR_NCOL];
-  const uint32_t nc = d.ctr[CTR_NC];
-  const uint32_t stride = gridDim.x * blockDim.x;
+// ---------------------------------------------------------------------------
+// Staging of the contact rows and impulses with bulk copies (TMA)
+// ---------------------------------------------------------------------------
+constexpr int kPgsThreads = 512;
+constexpr int kPerThread = 3;                        // contacts per thread per wave
+constexpr int kWave = kPgsThreads * kPerThread;      // contacts per wave
+constexpr int kStages = 2;                           // waves in flight
+// per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
+//              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
+constexpr size_t kRowBytes = 72;
+constexpr size_t kStageBytes = (size_t)kWave * kRowBytes;
+constexpr size_t kPgsSmem = kStages * kStageBytes;
+constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffLa = 48, kOffLb = 64;  // x kWave
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for a phase of a stage barrier; false (error latched) on timeout.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err) {
+  unsigned long long t0 = 0;
+  for (unsigned k = 0;; ++k) {
+    if (mbar_test(bar, parity)) return true;
+    if (k == 0) t0 = global_ns();
+    if ((k & 15u) == 15u && global_ns() - t0 > TDS_BARRIER_NS) {
+      latch_error(err, DEV_ERR_BARRIER);
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// This CTA's share [lo, hi) of colour col (its particle-pair bucket, padding,
+// then its static bucket), starting at a multiple of 4 contacts.
+__device__ __forceinline__ void colour_chunk(const DevPtrs &d, uint32_t col, uint32_t &lo, uint32_t &hi) {
+  const uint32_t s = d.bstart[2 * col], e = d.bend[2 * col + 1];
+  uint32_t q = (e - s + gridDim.x - 1) / gridDim.x;
+  q = (q + 3u) & ~3u;
+  lo = min(s + blockIdx.x * q, e);
+  hi = min(lo + q, e);
+}
+
+// Walks the (sweep, colour, wave) sequence of this CTA's staged waves.
+struct WaveSeq {
+  uint32_t sweep, col, w;
+  __device__ bool valid(uint32_t max_iters) const { return sweep < max_iters; }
+  // moves to the next wave, skipping colours without waves for this CTA
+  __device__ void advance(const uint32_t *nw, uint32_t ncol, uint32_t max_iters) {
+    ++w;
+    while (sweep < max_iters && w >= nw[col]) {
+      w = 0;
+      if (++col >= ncol) { col = 0; ++sweep; }
+    }
+  }
+};
+
+__device__ __forceinline__ void issue_wave(const DevPtrs &d, const WaveSeq &q, const uint32_t *lo,
+                                           const uint32_t *hi, unsigned char *stage,
+                                           unsigned long long *bar) {
+  const uint32_t p0 = lo[q.col] + q.w * kWave;
+  const uint32_t cnt = min((uint32_t)kWave, hi[q.col] - p0);
+  const uint32_t cnt2 = (cnt + 1u) & ~1u;  // 8-byte fields copied in pairs (16-byte multiples)
+  mbar_expect_tx(bar, 3u * 16u * cnt + 3u * 8u * cnt2);
+  bulk_g2s(stage + kOffAb * kWave, d.p_ab + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffRn * kWave, d.p_rn + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRq * kWave, d.p_rq + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRm * kWave, d.p_rm + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffLa * kWave, d.p_la + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffLb * kWave, d.p_lb + p0, 8u * cnt2, bar);
+}
+
+// The persistent solver: one CTA per SM, grid barrier between colours. The
+// rows and impulses of each wave (up to kWave contacts of one colour) are
+// staged in shared memory by bulk copies issued ahead, so they stream from
+// HBM while earlier colours are solved and barriers are crossed; each thread
+// then gathers both sides of its kPerThread contacts (through L2) before
+// solving any of them (contacts of one colour touch disjoint particles).
+__global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long full[kStages];
+  __shared__ uint32_t s_lo[TDS_MAX_COLOURS], s_hi[TDS_MAX_COLOURS], s_nw[TDS_MAX_COLOURS];
+  __shared__ double sh[kPgsThreads / 32];
+  __shared__ int s_flag;
+  __shared__ uint32_t s_waves;
+  const uint32_t ncol = min(d.ctr[CTR_NCOL], (uint32_t)TDS_MAX_COLOURS);
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  if (threadIdx.x == 0) s_waves = 0;
+  __syncthreads();
+  for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
+    colour_chunk(d, c, s_lo[c], s_hi[c]);
+    s_nw[c] = (s_hi[c] - s_lo[c] + kWave - 1) / kWave;
+    atomicAdd(&s_waves, s_nw[c]);
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kStages; ++k) mbar_init(&full[k], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint32_t waves_per_sweep = s_waves;
+  uint32_t gen = 0;  // grid barriers passed
+  // staged impulses of a wave were written one sweep earlier by this CTA, so
+  // never run further ahead than one sweep's worth of waves
+  const uint32_t ahead = min((uint32_t)kStages, waves_per_sweep);
+
   // v = M^-1 (p + G^T lambda_0), colour by colour (no conflicts inside one)
   if (a.apply_warm) {
     for (uint32_t col = 0; col < ncol; ++col) {
-      const uint32_t s = d.bucket_start[2 * col], e = d.bucket_start[2 * col + 2];
-      for (uint32_t p = s + tid; p < e; p += stride) {
-        float4 L0 = d.p_la[p];
-        float2 L1 = d.p_lb[p];
-        if (L0.x == 0.f && L0.y == 0.f && L0.z == 0.f && L0.w == 0.f && L1.x == 0.f && L1.y == 0.f)
-          continue;
-        Row r = load_row(d, p);
-        Side A, B;
-        load_pair(d, r, A, B);
-        float3 t1, t2;
-        onb(r.n, t1, t2);
-        apply(r, A, B, L0.x, L0.y * t1 + L0.z * t2, make_float3(L0.w, L1.x, L1.y));
-        store_side(d, r.ab.x, A);
-        if (r.dyn) store_side(d, r.ab.y, B);
+      for (int part = 0; part < 2; ++part) {
+        const uint32_t s = d.bstart[2 * col + part], e = d.bend[2 * col + part];
+        for (uint32_t p = s + tid; p < e; p += stride) {
+          float4 L0 = d.p_la[p];
+          float2 L1 = d.p_lb[p];
+          if (L0.x == 0.f && L0.y == 0.f && L0.z == 0.f && L0.w == 0.f && L1.x == 0.f && L1.y == 0.f)
+            continue;
+          Row r = load_row(d, p);
+          Side A, B;
+          load_pair(d, r, A, B);
+          float3 t1, t2;
+          onb(r.n, t1, t2);
+          apply(r, A, B, L0.x, L0.y * t1 + L0.z * t2, make_float3(L0.w, L1.x, L1.y));
+          store_side(d, r.ab.x, A);
+          if (r.dyn) store_side(d, r.ab.y, B);
+        }
       }
-      if (!grid_barrier(d.bar, d.err)) return;
+      if (!grid_barrier(d.bar, d.err, gen)) return;
     }
   }
+
+  // producer (thread 0): the next wave to stage
+  uint32_t issued = 0, consumed = 0;
+  WaveSeq prod{0, 0, 0xFFFFFFFFu};
+  if (waves_per_sweep > 0 && a.max_iters > 0) {
+    prod.advance(s_nw, ncol, a.max_iters);  // first wave
+    if (threadIdx.x == 0)
+      for (uint32_t k = 0; k < ahead && prod.valid(a.max_iters); ++k) {
+        issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
+                   &full[issued % kStages]);
+        ++issued;
+        prod.advance(s_nw, ncol, a.max_iters);
+      }
+  }
+
+  bool ok = true;
   uint32_t it = 0;
   float resid = -1.f;
-  while (it < a.max_iters) {
+  while (ok && it < a.max_iters) {
     for (uint32_t col = 0; col < ncol; ++col) {
-      const uint32_t s = d.bucket_start[2 * col], e = d.bucket_start[2 * col + 2];
-      for (uint32_t p = s + tid; p < e; p += stride) {
-        Row r = load_row(d, p);
-        float4 L0 = d.p_la[p];
-        float2 L1 = d.p_lb[p];
-        Side A, B;
-        load_pair(d, r, A, B);
-        pgs_update(r, A, B, L0, L1, a.sig_t, a.sig_r);
-        store_side(d, r.ab.x, A);
-        if (r.dyn) store_side(d, r.ab.y, B);
-        d.p_la[p] = L0;
-        d.p_lb[p] = L1;
+      for (uint32_t w = 0; w < s_nw[col]; ++w) {
+        const uint32_t st = consumed % kStages;
+        unsigned char *stage = smem + (size_t)st * kStageBytes;
+        if (!mbar_wait(&full[st], (consumed / kStages) & 1u, d.err)) { ok = false; break; }
+        const uint2 *sab = reinterpret_cast<const uint2 *>(stage + kOffAb * kWave);
+        const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
+        const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);
+        const float2 *srm = reinterpret_cast<const float2 *>(stage + kOffRm * kWave);
+        const float4 *sla = reinterpret_cast<const float4 *>(stage + kOffLa * kWave);
+        const float2 *slb = reinterpret_cast<const float2 *>(stage + kOffLb * kWave);
+        const uint32_t p0 = s_lo[col] + w * kWave;
+        const uint32_t cnt = min((uint32_t)kWave, s_hi[col] - p0);
+        Side A[kPerThread], B[kPerThread];
+        // gathers of every contact of this thread first (disjoint particles)
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+          const uint32_t li = j * kPgsThreads + threadIdx.x;
+          if (li < cnt) {
+            const uint2 ab = sab[li];
+            if (ab.x != 0xFFFFFFFFu) {  // not a padding slot
+              A[j] = load_side(d, ab.x);
+              if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
+              else B[j] = Side{f3(d.p_sv[p0 + li]), f3(d.p_sw[p0 + li]), 0.f, 0.f};
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+          const uint32_t li = j * kPgsThreads + threadIdx.x;
+          if (li < cnt) {
+            Row r;
+            r.ab = sab[li];
+            if (r.ab.x == 0xFFFFFFFFu) continue;
+            const float4 rn = srn[li], rq = srq[li];
+            const float2 rm = srm[li];
+            r.n = f3(rn); r.la = rn.w;
+            r.lb = rq.x; r.qn = rq.y; r.Sn = rq.z; r.fc = rq.w;
+            r.mu = rm.x; r.rmu = rm.y;
+            r.dyn = is_dyn(r.ab.y);
+            float4 L0 = sla[li];
+            float2 L1 = slb[li];
+            pgs_update(r, A[j], B[j], L0, L1, a.sig_t, a.sig_r);
+            store_side(d, r.ab.x, A[j]);
+            if (r.dyn) store_side(d, r.ab.y, B[j]);
+            d.p_la[p0 + li] = L0;
+            d.p_lb[p0 + li] = L1;
+          }
+        }
+        // impulses written above are read back by bulk copies one sweep later
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncthreads();  // the stage is free again
+        ++consumed;
+        if (threadIdx.x == 0 && prod.valid(a.max_iters)) {
+          issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
+                     &full[issued % kStages]);
+          ++issued;
+          prod.advance(s_nw, ncol, a.max_iters);
+        }
       }
-      if (!grid_barrier(d.bar, d.err)) return;
+      if (!ok) break;
+      if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
     }
+    if (!ok) break;
     ++it;
     if (it == a.max_iters || (a.tol > 0.f && it % a.every == 0)) {
       double num = 0.0, den = 0.0;
-      for (uint32_t p = tid; p < nc; p += stride) {
-        Row r = load_row(d, p);
-        Side A, B;
-        load_pair(d, r, A, B);
-        resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, num, den);
-      }
+      for (uint32_t col = 0; col < ncol; ++col)
+        for (int part = 0; part < 2; ++part)
+          for (uint32_t p = d.bstart[2 * col + part] + tid; p < d.bend[2 * col + part]; p += stride) {
+            Row r = load_row(d, p);
+            Side A, B;
+            load_pair(d, r, A, B);
+            resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, num, den);
+          }
       double bn = block_sum(num, sh);
       double bd = block_sum(den, sh);
       if (threadIdx.x == 0) {
         __stcg(d.dpart + 2 * blockIdx.x, bn);
         __stcg(d.dpart + 2 * blockIdx.x + 1, bd);
       }
-      if (!grid_barrier(d.bar, d.err)) return;
+      if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
       if (threadIdx.x == 0) {
         double tn = 0.0, td = 0.0;
         for (uint32_t b = 0; b < gridDim.x; ++b) {
@@ -240,17 +448,22 @@ __global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
           td += __ldcg(d.dpart + 2 * b + 1);
         }
         resid = (float)(sqrt(tn) / fmax(sqrt(td), 1e-12));
-        s_stop = a.tol > 0.f && resid <= a.tol;
+        s_flag = a.tol > 0.f && resid <= a.tol;
       }
       __syncthreads();
-      if (s_stop) break;
+      if (s_flag) break;
     }
   }
+  // drain the waves still in flight before the CTA exits
+  if (threadIdx.x == 0)
+    for (uint32_t q = consumed; q < issued; ++q)
+      if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err)) break;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint32_t nc = d.ctr[CTR_NC];
     d.ctr[CTR_ITERS] = it;
     d.fscal[FS_RESID] = resid;
     uint32_t nst = 0;
-    for (uint32_t c = 0; c < ncol; ++c) nst += d.bucket_start[2 * c + 2] - d.bucket_start[2 * c + 1];
+    for (uint32_t c = 0; c < ncol; ++c) nst += d.bend[2 * c + 1] - d.bstart[2 * c + 1];
     d.acc[ACC_SWEEP_PP] += (unsigned long long)it * (nc - nst);
     d.acc[ACC_SWEEP_ST] += (unsigned long long)it * nst;
     d.acc[ACC_CONTACTS] += nc;
@@ -262,9 +475,10 @@ __global__ void __launch_bounds__(256) k_pgs(DevPtrs d, SolveArgs a) {
 // impulses with the tangent in world coordinates); per particle id the range
 // of its owned contacts.
 __global__ void k_writeback(DevPtrs d) {
-  const uint32_t nc = d.ctr[CTR_NC];
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nc; p += gridDim.x * blockDim.x) {
+  const uint32_t np = d.ctr[CTR_PADDED];
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     uint32_t c = d.order[p];
+    if (c == 0xFFFFFFFFu) continue;  // padding slot
     float4 L0 = d.p_la[p];
     float2 L1 = d.p_lb[p];
     float3 n = f3(d.p_rn[p]), t1, t2;
@@ -289,7 +503,7 @@ __global__ void k_prev_ranges(DevPtrs d, uint32_t n, uint32_t cap) {
 
 __global__ void k_integrate(DevPtrs d, StepConsts k) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
-    float4 p = d.pos[i], v = d.vel[i], w = d.ang[i];
+    float4 p = d.pos[i], v = d.pv[2 * i], w = d.pv[2 * i + 1];
     p.x += k.dt * v.x;
     p.y += k.dt * v.y;
     p.z += k.dt * v.z;
@@ -307,10 +521,11 @@ __global__ void k_integrate(DevPtrs d, StepConsts k) {
 constexpr int kToolBlocks = 128;
 __global__ void k_tool_partial(DevPtrs d, StepConsts k) {
   __shared__ double sh[8];
-  const uint32_t nc = d.ctr[CTR_NC];
+  const uint32_t np = d.ctr[CTR_PADDED];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   const uint32_t first_tool = 1u + (uint32_t)k.n_walls;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < nc; p += gridDim.x * blockDim.x) {
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    if (d.order[p] == 0xFFFFFFFFu) continue;  // padding slot
     uint2 ab = d.p_ab[p];
     if (is_dyn(ab.y) || (ab.y & ~TDS_STATIC) < first_tool) continue;
     float4 rn = d.p_rn[p], L0 = d.p_la[p];
@@ -342,7 +557,7 @@ __global__ void k_tool_final(DevPtrs d) {
 __global__ void k_stage(DevPtrs d, uint32_t n) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t id = d.pid[i];
-    float4 p = d.pos[i], v = d.vel[i], w = d.ang[i];
+    float4 p = d.pos[i], v = d.pv[2 * i], w = d.pv[2 * i + 1];
     d.stage[0 * (size_t)n + id] = p.x; d.stage[1 * (size_t)n + id] = p.y;
     d.stage[2 * (size_t)n + id] = p.z; d.stage[3 * (size_t)n + id] = v.x;
     d.stage[4 * (size_t)n + id] = v.y; d.stage[5 * (size_t)n + id] = v.z;
@@ -370,7 +585,22 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
   DevPtrs dd = d;
   void *args[] = {&dd, &a};
-  return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(256), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(kPgsThreads), args,
+                                     kPgsSmem, st);
+}
+
+// Opt the solver into its shared-memory stages; returns the co-resident
+// blocks per SM for the cooperative launch.
+int tds_pgs_setup(int *threads) {
+  *threads = kPgsThreads;
+  if (cudaFuncSetAttribute((const void *)k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kPgsSmem) != cudaSuccess)
+    return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_pgs, kPgsThreads, kPgsSmem) !=
+      cudaSuccess)
+    return 0;
+  return occ;
 }
 
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st) {
@@ -386,4 +616,3 @@ void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st) {
   k_stage<<<grid_for(n, 256), 256, 0, st>>>(d, n);
 }
 
-const void *tds_pgs_kernel() { return (const void *)k_pgs; }

@@ -363,7 +363,7 @@ def large(seed: int = 0, n: int = 1000000) -> dict:
                     walls=bed_walls(8.0, 8.0, 8.0), tool_boxes=bucket())
     s = _spawned(p, n, 8.0, 8.0, 0.02, 0.03, seed, 0.0)
     s.update(name="large", steps=300, footprint=(8.0, 8.0), tool_kind="bucket",
-             settle_steps=300)
+             settle_steps=150)
     return s
 
 

@@ -26,7 +26,7 @@ STATIC_BIT = 0x80000000
 EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds_step",
             "tds_synchronize", "tds_read_particles", "tds_read_tool_force", "tds_read_contacts",
             "tds_get_stats", "tds_set_timing", "tds_set_solver", "tds_destroy_scene",
-            "tds_last_error"]
+            "tds_last_error", "tds_find_pair_contacts_noalloc"]
 
 
 class TdsError(RuntimeError):
@@ -66,7 +66,8 @@ class StepStats(ctypes.Structure):
                 ("steps", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
                 ("timed_steps", ctypes.c_uint32), ("phase_ms", ctypes.c_float * 5),
                 ("sweep_contacts_pp", ctypes.c_uint64), ("sweep_contacts_static", ctypes.c_uint64),
-                ("sum_contacts", ctypes.c_uint64), ("solved_steps", ctypes.c_uint64)]
+                ("sum_contacts", ctypes.c_uint64), ("solved_steps", ctypes.c_uint64),
+                ("colour_rounds", ctypes.c_uint32)]
 
 PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
 
@@ -95,6 +96,8 @@ def lib() -> ctypes.CDLL:
         L.tds_get_stats.argtypes = [vp, ctypes.POINTER(StepStats)]
         L.tds_set_timing.argtypes = [vp, ctypes.c_int32]
         L.tds_set_solver.argtypes = [vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint32]
+        L.tds_find_pair_contacts_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_int32,
+                                                     vp, ctypes.c_uint32, vp, vp]
         L.tds_destroy_scene.argtypes = [vp]
         L.tds_destroy_scene.restype = None
         L.tds_last_error.restype = ctypes.c_char_p
