@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--approach", type=float, default=0.3,
                     help="fraction of the dig path covered untimed before timing")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="residual mode: stop each step's solve at this residual (cap --max-iters)")
+    ap.add_argument("--max-iters", type=int, default=2000)
+    ap.add_argument("--cold", action="store_true", help="cold start instead of previous-step impulses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -165,6 +169,12 @@ def make_workload(args, rank: int) -> dict:
     scene = gen(seed=args.seed + rank, **kw)
     if args.iters:
         scene["iters"] = args.iters
+    if args.tol > 0:
+        scene["tol"] = args.tol
+        scene["iters"] = args.max_iters
+        scene["residual_every"] = 5
+    if args.cold:
+        scene["warm_start"] = 0
     return scene
 
 
@@ -176,6 +186,9 @@ def describe(scene: dict, args) -> dict:
                     f"{len(scene['tool_boxes'])}-box {scene['tool_kind']}, c_p {scene['cohesion']:g} Pa, "
                     f"{scene['iters']} PGS sweeps/step, previous-step warm start",
         "particles": int(len(scene["r"])), "sweeps": int(scene["iters"]), "dt": scene["dt"],
+        "solve": (f"residual <= {scene['tol']:g} (cap {scene['iters']} sweeps)" if scene.get("tol", 0) > 0
+                  else f"{scene['iters']} sweeps"),
+        "warm_start": "previous step" if scene.get("warm_start", 1) else "cold",
         "seed": args.seed, "l2": "inputs larger than L2 (contact rows and impulses > 129 MB)",
     }
 
@@ -382,6 +395,7 @@ def main():
         "config": {**describe(scene, args), "parallelism": f"replicas{world}" if world > 1 else "single",
                    "contacts_per_step": st["sum_contacts"] / max(1, st["solved_steps"]),
                    "colours": st["n_colours"], "colour_rounds": st["colour_rounds"],
+                   "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
                    "final_residual": st["residual"],
                    "phase_ms_per_step": {k: v / max(1, st["timed_steps"]) for k, v in st["phase_ms"].items()}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
