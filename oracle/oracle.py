@@ -76,7 +76,8 @@ def lib() -> ctypes.CDLL:
                                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                ctypes.c_int32, P(ctypes.c_uint64), P(ctypes.c_double),
                                ctypes.c_int32, P(ctypes.c_uint64), P(ctypes.c_double),
-                               P(ctypes.c_int32), P(ctypes.c_double), P(OrcStats)]
+                               P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double),
+                               P(ctypes.c_double), P(OrcStats)]
         L.orc_priority.restype = ctypes.c_uint64
         L.orc_priority.argtypes = [ctypes.c_uint64]
         dp = P(ctypes.c_double)
@@ -188,6 +189,8 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
         lam = np.zeros((cap, 7), dtype=np.float64)
         col = np.zeros(cap, dtype=np.int32)
         dl = np.zeros(cap, dtype=np.float64)
+        ft = np.zeros((cap, 10), dtype=np.float64)
+        tg = np.zeros((cap, 3), dtype=np.float64)
         x0, v0, w0 = state.x.copy(), state.v.copy(), state.w.copy()
         rc = lib().orc_step(ctypes.byref(P.c), n, _ptr(x0, ctypes.c_double),
                             _ptr(v0, ctypes.c_double), _ptr(w0, ctypes.c_double),
@@ -196,6 +199,7 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
                             _ptr(state.prev_lam, ctypes.c_double), cap,
                             _ptr(keys, ctypes.c_uint64), _ptr(lam, ctypes.c_double),
                             _ptr(col, ctypes.c_int32), _ptr(dl, ctypes.c_double),
+                            _ptr(ft, ctypes.c_double), _ptr(tg, ctypes.c_double),
                             ctypes.byref(st))
         if rc == -1:
             cap *= 2
@@ -209,7 +213,8 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
     state.prev_lam = lam[:nc].copy()
     return {
         "keys": keys[:nc].copy(), "lam": lam[:nc].copy(), "colour": col[:nc].copy(),
-        "delta": dl[:nc].copy(), "n_contacts": nc, "n_pp": st.n_pp, "n_static": st.n_static,
+        "delta": dl[:nc].copy(), "features": ft[:nc].copy(), "targets": tg[:nc].copy(),
+        "n_contacts": nc, "n_pp": st.n_pp, "n_static": st.n_static,
         "n_colours": st.n_colours, "iterations": st.iterations, "residual": st.residual,
         "tool_force": np.array(st.tool_force[:]), "tool_torque": np.array(st.tool_torque[:]),
     }

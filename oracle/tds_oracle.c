@@ -349,6 +349,10 @@ typedef struct {
   double st, sr;                  /* Sigma_bar of the tangent and rolling rows */
   double ln, lt[2], lr[3];        /* impulses */
   int colour;
+  int persisted;                  /* the key existed in the previous step */
+  double W;                       /* impulse scale m_eff |g| h of the learned warm start */
+  double sdir[3];                 /* slip direction s of the learned warm start */
+  double feat[10];
 } contact;
 
 typedef struct {
@@ -713,11 +717,111 @@ static uint64_t lcg_next(uint64_t *s) {
   return *s >> 33;
 }
 
+/* ------------------------------------------------------------------ */
+/* Learned warm start: per-contact features and the impulse scale      */
+/* ------------------------------------------------------------------ */
+/* Surface columns: the heightfield cells grouped f x f, f the smallest
+ * integer with f * cell >= 4 r_max; the surface of a column is the largest
+ * z + r of its particles (FP32, exact max). */
+static int column_of(const orc_params *P, int f, float px, float py, int ncx, int ncy) {
+  float w = P->hf_cell * (float)f;
+  float tx = (px - P->hf_x0) / w, ty = (py - P->hf_y0) / w;
+  float fx = floorf(tx), fy = floorf(ty);
+  int i, j;
+  if (!(fx >= 0.0f)) i = 0; else if (fx > (float)(ncx - 1)) i = ncx - 1; else i = (int)fx;
+  if (!(fy >= 0.0f)) j = 0; else if (fy > (float)(ncy - 1)) j = ncy - 1; else j = (int)fy;
+  return j * ncx + i;
+}
+
+int32_t orc_column_factor(const orc_params *P, int32_t n, const double *r) {
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) if ((double)(float)r[i] > rmax) rmax = (double)(float)r[i];
+  if (P->hf_nx <= 0 || !(P->hf_cell > 0.0f)) return 0;
+  int f = (int)ceil(4.0 * rmax / (double)P->hf_cell);
+  return f < 1 ? 1 : f;
+}
+
+/* Features (one row per contact, section "learned warm start" of the
+ * design): (J_n v^*) / (|g| h), delta/dbar, Lambda_n0/W, |Lambda_t0|/W,
+ * (Lambda_t0 . s)/W, persisted, Z_a, Z_b, depth below surface/dbar, type;
+ * W = m_eff |g| h with m_eff = 1/(1/m_a + 1/m_b); s = unit tangential slip
+ * velocity at v^* (or, below 1e-6 m/s, the unit n x e_k with e_k the axis
+ * least aligned with n). v and w hold v^* and w_n. */
+static int contact_features(const orc_params *P, int n, const double *x, const double *r,
+                            const masses *M, const double *v, const double *w, contact *C,
+                            int nc) {
+  double gn = sqrt(dot3(P->gravity, P->gravity));
+  double h = P->dt;
+  int *Z = (int *)calloc(n + 1, sizeof(int));
+  if (!Z) return -1;
+  for (int k = 0; k < nc; ++k) { Z[C[k].a]++; if (C[k].b >= 0) Z[C[k].b]++; }
+  int f = orc_column_factor(P, n, r), ncx = 0, ncy = 0;
+  float *surf = NULL;
+  if (f > 0) {
+    ncx = (P->hf_nx + f - 1) / f;
+    ncy = (P->hf_ny + f - 1) / f;
+    surf = (float *)malloc(sizeof(float) * ncx * ncy);
+    if (!surf) { free(Z); return -1; }
+    for (int q = 0; q < ncx * ncy; ++q) surf[q] = -INFINITY;
+    for (int i = 0; i < n; ++i) {
+      int col = column_of(P, f, (float)x[3 * i], (float)x[3 * i + 1], ncx, ncy);
+      float top = (float)x[3 * i + 2] + (float)r[i];
+      if (top > surf[col]) surf[col] = top;
+    }
+  }
+  for (int k = 0; k < nc; ++k) {
+    contact *c = &C[k];
+    double va[3], wa[3], vb[3], wb[3], u[3];
+    side_velocities(c, v, w, va, wa, vb, wb);
+    double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+    slip_velocity(c, va, wa, vb, wb, u);
+    double un = dot3(u, c->n);
+    double ut[3] = {u[0] - un * c->n[0], u[1] - un * c->n[1], u[2] - un * c->n[2]};
+    double ms = norm3(ut);
+    if (ms > 1e-6) {
+      for (int i = 0; i < 3; ++i) c->sdir[i] = ut[i] / ms;
+    } else {
+      int ax = 0;
+      double best = fabs(c->n[0]);
+      if (fabs(c->n[1]) < best) { best = fabs(c->n[1]); ax = 1; }
+      if (fabs(c->n[2]) < best) ax = 2;
+      double e[3] = {0.0, 0.0, 0.0}, t[3];
+      e[ax] = 1.0;
+      cross3(c->n, e, t);
+      double s = norm3(t);
+      for (int i = 0; i < 3; ++i) c->sdir[i] = t[i] / s;
+    }
+    double imb = c->b >= 0 ? M->m_inv[c->b] : 0.0;
+    c->W = gn * h / (M->m_inv[c->a] + imb);
+    double ra = r[c->a], dbar = c->b >= 0 ? ra + r[c->b] : 2.0 * ra;
+    double lt[3];
+    for (int i = 0; i < 3; ++i) lt[i] = c->lt[0] * c->t1[i] + c->lt[1] * c->t2[i];
+    double depth = 0.0;
+    if (surf) {
+      int col = column_of(P, f, (float)x[3 * c->a], (float)x[3 * c->a + 1], ncx, ncy);
+      depth = ((double)surf[col] - x[3 * c->a + 2]) / dbar;
+    }
+    c->feat[0] = dot3(c->n, dv) / (gn * h);
+    c->feat[1] = c->delta / dbar;
+    c->feat[2] = c->ln / c->W;
+    c->feat[3] = norm3(lt) / c->W;
+    c->feat[4] = dot3(lt, c->sdir) / c->W;
+    c->feat[5] = c->persisted ? 1.0 : 0.0;
+    c->feat[6] = (double)Z[c->a];
+    c->feat[7] = c->b >= 0 ? (double)Z[c->b] : 0.0;
+    c->feat[8] = depth;
+    c->feat[9] = c->b >= 0 ? 0.0 : (c->is_tool ? 2.0 : 1.0);
+  }
+  free(surf);
+  free(Z);
+  return 0;
+}
+
 int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w,
                  const double *r, int32_t n_prev, const uint64_t *prev_keys,
                  const double *prev_lam, int32_t cap, uint64_t *out_keys,
                  double *out_lam, int32_t *out_colour, double *out_delta,
-                 orc_stats *st) {
+                 double *out_feat, double *out_targ, orc_stats *st) {
   if (!P || n < 0 || cap < 0 || !st || (n > 0 && (!x || !v || !w || !r))) return -2;
   if (n_prev > 0 && (!prev_keys || !prev_lam)) return -2;
   memset(st, 0, sizeof(*st));
@@ -771,7 +875,7 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     contact_rows(P, r, &M, v0, c);
   }
   free(v0);
-  /* 2. p = M v_n + h f: v* = v_n + h g (gravity is the only external force) */
+  /* 2. p = M v_n + h f: v^* = v_n + h g (gravity is the only external force) */
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < 3; ++k) v[3 * i + k] += h * P->gravity[k];
   /* 3. warm start: previous impulses by key, Lambda_t re-projected onto the
@@ -783,6 +887,7 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     int j = find_key(n_prev, prev_keys, c->key);
     if (j < 0) continue;
     const double *pl = prev_lam + 7 * j;
+    c->persisted = 1;
     c->ln = pl[0] < -c->fc ? -c->fc : pl[0];
     double tw[3] = {pl[1], pl[2], pl[3]};
     c->lt[0] = dot3(c->t1, tw);
@@ -790,6 +895,12 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     project_ball(c->lt, 2, c->mu * fabs(c->ln));
     for (int i = 0; i < 3; ++i) c->lr[i] = pl[4 + i];
     project_ball(c->lr, 3, c->rmu * fabs(c->ln));
+  }
+  /* learned-warm-start features of every contact at v* with lambda_0 */
+  if (contact_features(P, n, x, r, &M, v, w, C, nc)) { rc = -2; goto done; }
+  for (int k = 0; k < nc; ++k) {
+    contact *c = &C[k];
+    if (!c->persisted) continue;
     double tw0[3] = {c->lt[0] * c->t1[0] + c->lt[1] * c->t2[0],
                      c->lt[0] * c->t1[1] + c->lt[1] * c->t2[1],
                      c->lt[0] * c->t1[2] + c->lt[1] * c->t2[2]};
@@ -865,6 +976,16 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     }
     if (out_colour) out_colour[k] = c->colour;
     if (out_delta) out_delta[k] = c->delta;
+    if (out_feat)
+      for (int i = 0; i < 10; ++i) out_feat[10 * k + i] = c->feat[i];
+    if (out_targ) {
+      double lt[3], nxs[3];
+      for (int i = 0; i < 3; ++i) lt[i] = c->lt[0] * c->t1[i] + c->lt[1] * c->t2[i];
+      cross3(c->n, c->sdir, nxs);
+      out_targ[3 * k + 0] = c->ln / c->W;
+      out_targ[3 * k + 1] = dot3(lt, c->sdir) / c->W;
+      out_targ[3 * k + 2] = dot3(lt, nxs) / c->W;
+    }
   }
 done:
   free(B); free(M.m_inv); free(M.I_inv); free(keys); free(C); free(order); free(cstart);

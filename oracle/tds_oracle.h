@@ -90,7 +90,23 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
                  const double *r, int32_t n_prev, const uint64_t *prev_keys,
                  const double *prev_lam, int32_t cap, uint64_t *out_keys,
                  double *out_lam, int32_t *out_colour, double *out_delta,
-                 orc_stats *st);
+                 double *out_feat, double *out_targ, orc_stats *st);
+
+/* Learned warm start. out_feat (10 per contact) and out_targ (3 per contact)
+ * of orc_step, in key order:
+ *   features: (J_n v^*) / (|g| h), delta/dbar, Lambda_n0/W, |Lambda_t0|/W,
+ *             (Lambda_t0 . s)/W, persisted (0/1), Z_a, Z_b (0 static),
+ *             depth below the surface / dbar, type (0 pair, 1 terrain or wall,
+ *             2 tool);
+ *   targets:  Lambda_n/W, (Lambda_t . s)/W, (Lambda_t . (n x s))/W of the
+ *             step's final impulses;
+ * with W = |g| h / (1/m_a + 1/m_b), dbar = r_a + r_b (static 2 r_a), lambda_0
+ * the previous-step impulses as the warm start sets them, v^* = v_n + h g, s
+ * the unit tangential slip velocity at v^* (below 1e-6 m/s: unit n x e_k, e_k
+ * the axis least aligned with n). Surface columns are the heightfield cells
+ * grouped f x f (orc_column_factor), the surface of a column the largest
+ * FP32 z + r of its particles. */
+int32_t orc_column_factor(const orc_params *P, int32_t n, const double *r);
 
 /* The SplitMix64 finaliser used as the colouring priority of a key. */
 uint64_t orc_priority(uint64_t key);

@@ -431,3 +431,99 @@ def test_warm_start_restart_is_stationary(orc):
     res2 = orc.step(s, st, iters=1, tol=0.0)
     assert res2["residual"] < 1e-8
     np.testing.assert_allclose(res2["lam"][:, 0], res["lam"][:, 0], rtol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# learned warm start: features and targets of the oracle
+# --------------------------------------------------------------------------
+
+def test_learned_features_and_targets_of_a_resting_column(orc):
+    """K equal spheres at rest on flat ground: pair contact j from the top
+    carries j m g h, so its target Lambda_n/W with W = (m/2) g h is 2j, the
+    ground contact's (W = m g h) is K; coordination numbers, depth below the
+    column top, types and the predicted normal velocity follow from the
+    geometry: pairs fall together (0), the ground contact approaches at g h
+    (feature -1)."""
+    K, r = 4, 0.05
+    x = [[0.0, 0.0, r + 2 * r * k] for k in range(K)]
+    s = S.with_particles(S.base_params(hf=S.flat_heightfield(4, 4, -1, -1, 0.5), mu_t=0.5,
+                                       iters=400, tol=1e-12, residual_every=5), x, [r] * K)
+    st, res = run(orc, s, 300)
+    F, T, keys = res["features"], res["targets"], res["keys"]
+    for j in range(1, K):
+        a = K - 1 - j
+        i = int(np.nonzero(keys == ((a << 32) | (a + 1)))[0][0])
+        assert T[i, 0] == pytest.approx(2.0 * j, rel=1e-6)
+        assert F[i, 2] == pytest.approx(2.0 * j, rel=1e-6)  # previous impulse, converged
+        assert abs(F[i, 0]) < 1e-6 and F[i, 5] == 1.0 and F[i, 9] == 0.0
+        assert F[i, 6] == 2 and F[i, 7] == (1 if a + 1 == K - 1 else 2)
+        assert F[i, 8] == pytest.approx(K - a - 0.5, abs=0.01)  # (top - z_a) / 2r, top = 2 r K
+        assert F[i, 1] == pytest.approx(res["delta"][i] / (2 * r), rel=1e-6)
+        assert abs(T[i, 1]) < 1e-6 and abs(T[i, 2]) < 1e-6
+    g = int(np.nonzero(keys == ((0 << 32) | S_BIT))[0][0])
+    assert T[g, 0] == pytest.approx(K, rel=1e-6)
+    assert F[g, 0] == pytest.approx(-1.0, rel=1e-6)
+    assert F[g, 9] == 1.0 and F[g, 7] == 0.0 and F[g, 6] == 2
+    assert F[g, 8] == pytest.approx(K - 0.5, abs=0.01)  # the column holds all spheres
+
+
+def test_learned_friction_target_opposes_the_slip(orc):
+    """A sphere sliding on flat ground (rolling locked): the friction impulse
+    is mu Lambda_n against the slip, so target (Lambda_t . s)/W = -mu x target
+    Lambda_n/W, and the normal target is 1 (W = m g h)."""
+    r, mu = 0.05, 0.3
+    s = S.with_particles(S.base_params(hf=S.flat_heightfield(100, 4, -1, -0.2, 0.1), mu_t=mu,
+                                       mu_r=100.0, iters=60), [[0.0, 0.0, r]], [r])
+    st = orc.State(s)
+    for _ in range(60):
+        orc.step(s, st)
+    st.v[0, 0] = 2.0
+    res = orc.step(s, st)
+    res = orc.step(s, st)
+    T, F = res["targets"][0], res["features"][0]
+    assert T[0] == pytest.approx(1.0, rel=1e-3)
+    assert T[1] == pytest.approx(-mu * T[0], rel=1e-6)
+    assert abs(T[2]) < 1e-9
+    assert F[4] == pytest.approx(-mu * F[2], rel=1e-6)  # previous friction also opposed the slip
+
+
+def _mlp_params(seed):
+    g = S.rng(seed)
+    return {"W1": g.normal(0, 0.4, (64, 10)), "b1": g.normal(0, 0.1, 64),
+            "W2": g.normal(0, 0.2, (64, 64)), "b2": g.normal(0, 0.1, 64),
+            "W3": g.normal(0, 0.2, (3, 64)), "b3": g.normal(0, 0.1, 3)}
+
+
+def test_mlp_backward_matches_finite_differences(orc):
+    """The oracle's analytic FP64 gradients of the MSE loss against central
+    differences (step 1e-6) on a 64-sample batch, for every parameter tensor."""
+    g = S.rng(5)
+    X = g.normal(0, 1, (64, 10))
+    T = g.normal(0, 1, (64, 3))
+    p = _mlp_params(6)
+    loss, grads = orc.mlp_loss_grad(X, T, p)
+    assert loss > 0
+    for name, arr in p.items():
+        flat = arr.reshape(-1)
+        idx = S.rng(7).choice(flat.size, size=min(12, flat.size), replace=False)
+        for i in idx:
+            q = {k: v.copy() for k, v in p.items()}
+            eps = 1e-6
+            q[name].reshape(-1)[i] = flat[i] + eps
+            lp, _ = orc.mlp_loss_grad(X, T, q)
+            q[name].reshape(-1)[i] = flat[i] - eps
+            lm, _ = orc.mlp_loss_grad(X, T, q)
+            fd = (lp - lm) / (2 * eps)
+            an = grads[name].reshape(-1)[i]
+            assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + 1e-9, (name, i, fd, an)
+
+
+def test_mlp_forward_is_the_layer_formula(orc):
+    """Forward pass against the three layers written with numpy matmuls."""
+    g = S.rng(8)
+    X = g.normal(0, 1, (32, 10))
+    p = _mlp_params(9)
+    Y = orc.mlp_forward(X, p)
+    h1 = np.maximum(X @ p["W1"].T + p["b1"], 0)
+    h2 = np.maximum(h1 @ p["W2"].T + p["b2"], 0)
+    np.testing.assert_allclose(Y, h2 @ p["W3"].T + p["b3"], rtol=1e-12, atol=1e-12)
