@@ -57,7 +57,7 @@ typedef enum {
   TDS_ERR_STATE = -7            /* the scene already holds an error */
 } tds_status;
 
-typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1 } tds_warm_start;
+typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1, TDS_WARM_LEARNED = 2 } tds_warm_start;
 
 /* Scene description. All pointers are host pointers, read during
  * tds_create_scene only.
@@ -154,6 +154,10 @@ tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[
  * residual mode), tol (> 0: residual mode) and the residual check period. */
 tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t residual_every);
 
+/* Change the warm start (tds_warm_start) for the following steps;
+ * TDS_WARM_LEARNED needs tds_set_mlp_weights before the next step. */
+tds_status tds_set_warm_start(tds_scene *s, int32_t mode);
+
 /* Advance nsteps time steps (asynchronous). */
 tds_status tds_step(tds_scene *s, uint32_t nsteps);
 
@@ -188,6 +192,57 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out);
 tds_status tds_set_timing(tds_scene *s, int32_t enable);
 
 void tds_destroy_scene(tds_scene *s);
+
+/* ---- learned warm start ------------------------------------------------------
+ * Not in the paper, whose discussion proposes data-driven models trained on
+ * resolved simulations as future work: a 10 -> 64 -> 64 -> 3 ReLU network
+ * predicts each contact's initial normal and friction impulses; projected
+ * Gauss-Seidel then solves as usual (it reaches the same residual; only the
+ * sweep count changes). Inputs per contact (10): (J_n v*)/(|g| h),
+ * overlap/(r_a + r_b), the previous step's normal, |tangent| and
+ * slip-aligned tangent impulse over W, persisted (0/1), coordination numbers
+ * of both particles, depth below the local surface / (r_a + r_b), contact
+ * type (0 pair, 1 terrain or wall, 2 tool); W = |g| h / (1/m_a + 1/m_b),
+ * v* = v_n + h g, s the unit tangential slip velocity at v* (below 1e-6 m/s:
+ * unit n x e_k, e_k the axis least aligned with n), surface = largest z + r
+ * in columns of f x f heightfield cells with f the smallest integer such that
+ * f * cell >= 4 r_max. Outputs (3): Lambda_n/W, (Lambda_t . s)/W,
+ * (Lambda_t . (n x s))/W. BF16 weights, FP32 accumulation (tensor cores).
+ * Parameters: FP32 vector of tds_mlp_param_count() floats, row-major
+ * W1[64][10], b1[64], W2[64][64], b2[64], W3[3][64], b3[3]. */
+uint32_t tds_mlp_param_count(void);
+
+/* Weights used by a scene created with warm_start = TDS_WARM_LEARNED (host
+ * FP32 parameters, copied). Waits. */
+tds_status tds_set_mlp_weights(tds_scene *s, const float *params, uint32_t count);
+
+/* Record training data: with recording on, every step keeps each contact's
+ * features (at the start of the step) and targets (its final impulses in the
+ * output units above). */
+tds_status tds_set_recording(tds_scene *s, int32_t enable);
+
+/* The last recorded step's samples in owner order: feat 10 floats, targ 3
+ * floats and key (as in tds_read_contacts) per contact, at most cap of them;
+ * *count receives the total. Host pointers (any may be NULL). Waits. */
+tds_status tds_read_training_samples(tds_scene *s, float *feat, float *targ, uint64_t *keys,
+                                     uint32_t cap, uint32_t *count);
+
+/* Device-buffer network calls for training (all pointers device memory,
+ * stream a cudaStream_t or NULL; asynchronous). workspace holds
+ * tds_mlp_workspace_bytes() bytes (the packed BF16 weights).
+ * tds_mlp_forward: Y[m][3] of X[m][10].
+ * tds_mlp_loss_grad: loss = (1/(3m)) sum (y - T)^2 into *loss and its
+ *   gradient with respect to params into grad (both overwritten).
+ * tds_mlp_adam_step: Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected
+ *   with the 1-based step) on the FP32 params with moments mom, vel; zeroes
+ *   grad. */
+tds_status tds_mlp_workspace_bytes(uint64_t *bytes);
+tds_status tds_mlp_forward(const float *params, const float *X, uint32_t m, float *Y,
+                           void *workspace, void *stream);
+tds_status tds_mlp_loss_grad(const float *params, const float *X, const float *T, uint32_t m,
+                             float *grad, float *loss, void *workspace, void *stream);
+tds_status tds_mlp_adam_step(float *params, float *grad, float *mom, float *vel, uint32_t step,
+                             float lr, void *stream);
 
 /* ---- particle-pair contacts without any allocation -------------------------
  * The paper has no counterpart to this call; it serves callers that cannot

@@ -14,6 +14,18 @@ int tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells
 int tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st);
 int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
                          int coop_threads, cudaStream_t st);
+int tds_launch_bucketing(const DevPtrs &d, uint32_t cap, cudaStream_t st);
+void tds_launch_features(const DevPtrs &d, const StepConsts &k, const MlpConsts &q, int *surf,
+                         uint32_t cap, cudaStream_t st);
+void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, cudaStream_t st);
+size_t tds_mlp_packed_bytes();
+int tds_mlp_params();
+void tds_mlp_pack(const float *params, void *packed, cudaStream_t st);
+void tds_mlp_forward_launch(const void *packed, const float *X, uint32_t m, float *Y, cudaStream_t st);
+cudaError_t tds_mlp_loss_grad_launch(const void *packed, const float *X, const float *T, uint32_t m,
+                                     float *grad, float *loss, cudaStream_t st);
+void tds_mlp_adam_launch(float *params, float *grad, float *mom, float *vel, uint32_t step, float lr,
+                         cudaStream_t st);
 int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
                            uint32_t every, int apply_warm, int blocks, cudaStream_t st);
@@ -73,6 +85,15 @@ struct Sizes {
   uint32_t n, cap, ncells, ntiles, hf_words;
   int gnx, gny, gnz;
   float lo[3], cell;
+  MlpConsts mq;  // surface columns of the learned warm start
+};
+
+struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
+  float *hf = nullptr;
+  int *surf = nullptr;
+  void *packed = nullptr;
+  float *params = nullptr;
+  float *targ = nullptr;
 };
 
 }  // namespace
@@ -96,6 +117,8 @@ struct tds_scene {
   bool timing = false;
   std::vector<cudaEvent_t> ev;  // 6 per timed step
   size_t ev_used = 0;
+  Extra x;
+  bool recording = false, have_weights = false;
 };
 
 namespace {
@@ -116,8 +139,8 @@ tds_status validate(const tds_scene_desc *d) {
   if (d->hf_nx > 0 && (d->hf_ny == 0 || !d->hf_heights || !(d->hf_cell > 0.f)))
     return fail(TDS_ERR_INVALID_ARG, "heightfield needs ny > 0, heights and cell > 0");
   if (d->max_iters == 0) return fail(TDS_ERR_INVALID_ARG, "max_iters must be >= 1");
-  if (d->warm_start != TDS_WARM_COLD && d->warm_start != TDS_WARM_PREV)
-    return fail(TDS_ERR_INVALID_ARG, "warm_start must be TDS_WARM_COLD or TDS_WARM_PREV");
+  if (d->warm_start != TDS_WARM_COLD && d->warm_start != TDS_WARM_PREV && d->warm_start != TDS_WARM_LEARNED)
+    return fail(TDS_ERR_INVALID_ARG, "warm_start must be TDS_WARM_COLD, TDS_WARM_PREV or TDS_WARM_LEARNED");
   for (uint32_t i = 0; i < d->n; ++i)
     if (!(d->radius[i] > 0.f) || !std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) ||
         !std::isfinite(d->z[i]))
@@ -182,10 +205,20 @@ Sizes plan(const tds_scene_desc *d) {
   s.ncells = (uint32_t)((uint64_t)dims[0] * dims[1] * dims[2]);
   for (int a = 0; a < 3; ++a) s.lo[a] = lo[a];
   s.hf_words = d->hf_nx > 0 ? (d->hf_nx + 1) * (d->hf_ny + 1) : 1;
+  // surface columns: heightfield cells grouped cf x cf, cf the smallest
+  // integer with cf * cell >= 4 r_max
+  s.mq = MlpConsts{0, 1, 1};
+  if (d->hf_nx > 0) {
+    int cf = (int)std::ceil(4.0 * (double)rmax / (double)d->hf_cell);
+    if (cf < 1) cf = 1;
+    s.mq.cf = cf;
+    s.mq.ncx = ((int)d->hf_nx + cf - 1) / cf;
+    s.mq.ncy = ((int)d->hf_ny + cf - 1) / cf;
+  }
   return s;
 }
 
-size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) {
+size_t carve(Carver &c, const Sizes &s, DevPtrs &d, Extra &x, int pgs_blocks) {
   const uint32_t n = s.n, cap = s.cap;
   d.pos = c.take<float4>(n); d.pv = c.take<float4>(2 * (size_t)n);
   d.pid = c.take<uint32_t>(n);
@@ -244,7 +277,14 @@ size_t carve(Carver &c, const Sizes &s, DevPtrs &d, float **hf, int pgs_blocks) 
   d.scan_tmp = c.take<uint32_t>(tds_scan_tmp_words((uint32_t)m));
   d.stage = c.take<float>(9 * (size_t)n);
   d.tool_out = c.take<float>(6);
-  *hf = c.take<float>(s.hf_words);
+  d.feat = c.take<float>(10 * (size_t)cap);
+  d.sdirw = c.take<float4>(cap);
+  d.c_flag = c.take<uint8_t>(cap);
+  x.targ = c.take<float>(3 * (size_t)cap);
+  x.surf = c.take<int>((size_t)s.mq.ncx * s.mq.ncy);
+  x.packed = c.take<unsigned char>(tds_mlp_packed_bytes());
+  x.params = c.take<float>(tds_mlp_params());
+  x.hf = c.take<float>(s.hf_words);
   return c.off + 256;
 }
 
@@ -334,11 +374,11 @@ tds_status tds_workspace_bytes(const tds_scene_desc *desc, uint64_t *bytes) {
   if (!bytes) return fail(TDS_ERR_INVALID_ARG, "bytes is NULL");
   Sizes s = plan(desc);
   DevPtrs d{};
-  float *hf;
+  Extra x;
   Carver c{nullptr};
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  *bytes = carve(c, s, d, &hf, 64 * sms);
+  *bytes = carve(c, s, d, x, 64 * sms);
   return TDS_OK;
 }
 
@@ -368,10 +408,10 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
   }
   s->pgs_blocks = pgs_blocks_for(desc->n, sms);  // one co-resident CTA per SM at most
   s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
-  float *hf = nullptr;
   Carver probe{nullptr};
   DevPtrs tmp{};
-  size_t need = carve(probe, s->sz, tmp, &hf, 64 * sms);
+  Extra tx;
+  size_t need = carve(probe, s->sz, tmp, tx, 64 * sms);
   if (workspace) {
     if (workspace_bytes < need) {
       delete s;
@@ -387,7 +427,9 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
     s->owns = true;
   }
   Carver c{(char *)s->mem};
-  carve(c, s->sz, s->d, &hf, 64 * sms);
+  carve(c, s->sz, s->d, s->x, 64 * sms);
+  float *hf = s->x.hf;
+  s->d.targ = nullptr;
   // constants
   StepConsts &k = s->k;
   std::memset(&k, 0, sizeof(k));
@@ -479,10 +521,20 @@ tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t 
   return TDS_OK;
 }
 
+tds_status tds_set_warm_start(tds_scene *s, int32_t mode) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (mode != TDS_WARM_COLD && mode != TDS_WARM_PREV && mode != TDS_WARM_LEARNED)
+    return fail(TDS_ERR_INVALID_ARG, "unknown warm start");
+  s->desc.warm_start = mode;
+  return TDS_OK;
+}
+
 tds_status tds_step(tds_scene *s, uint32_t nsteps) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
   tds_status ls = check_latched(s);
   if (ls != TDS_OK) return ls;
+  if (s->desc.warm_start == TDS_WARM_LEARNED && !s->have_weights)
+    return fail(TDS_ERR_STATE, "TDS_WARM_LEARNED needs tds_set_mlp_weights first");
   const tds_scene_desc &D = s->desc;
   for (uint32_t it = 0; it < nsteps; ++it) {
     DevPtrs &d = s->d;
@@ -502,13 +554,25 @@ tds_status tds_step(tds_scene *s, uint32_t nsteps) {
     std::swap(d.pv, d.pv2);
     std::swap(d.pid, d.pid2);
     if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
-    int use_prev = (D.warm_start == TDS_WARM_PREV) && s->have_prev;
+    const bool learned = D.warm_start == TDS_WARM_LEARNED;
+    // the learned warm start also reads the previous step's impulses
+    int use_prev = (D.warm_start != TDS_WARM_COLD) && s->have_prev;
     s->launches += tds_launch_narrowphase(d, s->k, use_prev, s->st);
     s->launches += tds_launch_predict(d, s->k, s->st);
     if (E) CUDA_TRY(cudaEventRecord(E[2], s->st));
     s->launches += tds_launch_colouring(d, s->sz.n, s->sz.cap, s->colour_blocks, 256, s->st);
+    d.targ = s->recording ? s->x.targ : nullptr;
+    if (learned || s->recording) {
+      tds_launch_features(d, s->k, s->sz.mq, s->x.surf, s->sz.cap, s->st);
+      s->launches += s->sz.mq.cf > 0 ? 3 : 1;
+    }
+    if (learned) {
+      tds_launch_learned(d, s->x.packed, s->sz.cap, s->st);
+      s->launches += 1;
+    }
+    s->launches += tds_launch_bucketing(d, s->sz.cap, s->st);
     if (E) CUDA_TRY(cudaEventRecord(E[3], s->st));
-    CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev,
+    CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned,
                             s->pgs_blocks, s->st));
     s->launches += 1;
     if (E) CUDA_TRY(cudaEventRecord(E[4], s->st));
@@ -643,6 +707,82 @@ tds_status tds_read_contacts(tds_scene *s, uint64_t *keys, float *lam, uint32_t 
       o[0] = l0[i].x; o[1] = l0[i].y; o[2] = l0[i].z; o[3] = l0[i].w;
       o[4] = l1[i].x; o[5] = l1[i].y; o[6] = l1[i].z;
     }
+  return TDS_OK;
+}
+
+tds_status tds_set_mlp_weights(tds_scene *s, const float *params, uint32_t count) {
+  if (!s || !params) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if ((int)count != tds_mlp_params()) return fail(TDS_ERR_INVALID_ARG, "count must be tds_mlp_param_count()");
+  CUDA_TRY(cudaMemcpyAsync(s->x.params, params, sizeof(float) * count, cudaMemcpyHostToDevice, s->st));
+  tds_mlp_pack(s->x.params, s->x.packed, s->st);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  s->have_weights = true;
+  return TDS_OK;
+}
+
+tds_status tds_set_recording(tds_scene *s, int32_t enable) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  s->recording = enable != 0;
+  return TDS_OK;
+}
+
+tds_status tds_read_training_samples(tds_scene *s, float *feat, float *targ, uint64_t *keys,
+                                     uint32_t cap, uint32_t *count) {
+  if (!s || !count) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  if (!s->recording) return fail(TDS_ERR_STATE, "recording is off (tds_set_recording)");
+  uint32_t nc = 0;
+  CUDA_TRY(cudaMemcpyAsync(&nc, s->d.ctr + CTR_NC, sizeof(nc), cudaMemcpyDeviceToHost, s->st));
+  tds_status r = sync_and_check(s);
+  if (r != TDS_OK) return r;
+  *count = nc;
+  uint32_t m = nc < cap ? nc : cap;
+  if (m == 0 || s->steps == 0) return TDS_OK;
+  if (feat) CUDA_TRY(cudaMemcpyAsync(feat, s->d.feat, sizeof(float) * 10 * m, cudaMemcpyDeviceToHost, s->st));
+  if (targ) CUDA_TRY(cudaMemcpyAsync(targ, s->x.targ, sizeof(float) * 3 * m, cudaMemcpyDeviceToHost, s->st));
+  if (keys) CUDA_TRY(cudaMemcpyAsync(keys, s->d.c_key, sizeof(uint64_t) * m, cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  return TDS_OK;
+}
+
+uint32_t tds_mlp_param_count(void) { return (uint32_t)tds_mlp_params(); }
+
+tds_status tds_mlp_workspace_bytes(uint64_t *bytes) {
+  if (!bytes) return fail(TDS_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = tds_mlp_packed_bytes();
+  return TDS_OK;
+}
+
+tds_status tds_mlp_forward(const float *params, const float *X, uint32_t m, float *Y, void *workspace,
+                           void *stream) {
+  if (!params || !X || !Y || !workspace) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  tds_mlp_pack(params, workspace, st);
+  if (m) tds_mlp_forward_launch(workspace, X, m, Y, st);
+  CUDA_TRY(cudaGetLastError());
+  return TDS_OK;
+}
+
+tds_status tds_mlp_loss_grad(const float *params, const float *X, const float *T, uint32_t m, float *grad,
+                             float *loss, void *workspace, void *stream) {
+  if (!params || !X || !T || !grad || !loss || !workspace) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (m == 0) return fail(TDS_ERR_INVALID_ARG, "m must be >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * tds_mlp_params(), st));
+  CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  tds_mlp_pack(params, workspace, st);
+  CUDA_TRY(tds_mlp_loss_grad_launch(workspace, X, T, m, grad, loss, st));
+  return TDS_OK;
+}
+
+tds_status tds_mlp_adam_step(float *params, float *grad, float *mom, float *vel, uint32_t step, float lr,
+                             void *stream) {
+  if (!params || !grad || !mom || !vel) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (step == 0 || !(lr > 0.f)) return fail(TDS_ERR_INVALID_ARG, "step >= 1 and lr > 0 required");
+  tds_mlp_adam_launch(params, grad, mom, vel, step, lr, (cudaStream_t)stream);
+  CUDA_TRY(cudaGetLastError());
   return TDS_OK;
 }
 

@@ -263,13 +263,18 @@ int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_bl
   void *args[] = {&dd};
   cudaLaunchCooperativeKernel((const void *)k_colour_rounds, dim3(coop_blocks), dim3(coop_threads),
                               args, 0, st);
+  return 8;
+}
+
+// Contact rows (and initial impulses) into the padded colour order.
+int tds_launch_bucketing(const DevPtrs &d, uint32_t cap, cudaStream_t st) {
   k_bucket_hist<<<d.ntiles, 256, 0, st>>>(d);
   tds_scan_exclusive(d.tile_hist, d.tile_off, TDS_NBUCKETS * d.ntiles, d.scan_tmp, st);
   k_bucket_starts<<<1, 32, 0, st>>>(d);
   cudaMemsetAsync(d.order, 0xFF, sizeof(uint32_t) * ((size_t)cap + TDS_ORDER_PAD), st);
   cudaMemsetAsync(d.p_ab, 0xFF, sizeof(uint2) * ((size_t)cap + TDS_ORDER_PAD), st);  // padding sentinel
   k_bucket_scatter<<<d.ntiles, 256, 0, st>>>(d);
-  return 12;
+  return 4;
 }
 
 const void *tds_colour_kernel() { return (const void *)k_colour_rounds; }

@@ -254,6 +254,7 @@ struct Writer {
     // onto the new tangent plane, everything clamped into the new bounds
     float4 la0 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 lb0 = make_float2(0.f, 0.f);
+    uint8_t persisted = 0;
     if (use_prev) {
       for (uint32_t q = pf; q < pf + pc; ++q) {
         if (__ldg(d.prev_other[0] + q) != other) continue;
@@ -270,11 +271,13 @@ struct Writer {
         if (mr > br) lr = (br > 0.f ? br / mr : 0.f) * lr;
         la0 = make_float4(ln, a1, a2, lr.x);
         lb0 = make_float2(lr.y, lr.z);
+        persisted = 1;
         break;
       }
     }
     d.c_la[c] = la0;
     d.c_lb[c] = lb0;
+    d.c_flag[c] = persisted;
   }
 
   __device__ void pair(uint32_t j, uint32_t pj, float4 Q) {

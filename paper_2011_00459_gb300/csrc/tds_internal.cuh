@@ -102,6 +102,17 @@ struct DevPtrs {
   uint32_t *scan_tmp;
   float *stage;               // 9 n floats for reads
   float *tool_out;            // 6 floats
+  // learned warm start (owner order)
+  float *feat;                // 10 features per contact
+  float4 *sdirw;              // slip direction s and impulse scale W per contact
+  float *targ;                // 3 targets per contact (recording)
+  uint8_t *c_flag;            // 1 if the contact's key existed in the previous step
+};
+
+// Surface columns of the learned warm start's depth feature: heightfield
+// cells grouped cf x cf (cf = 0: no heightfield, depth 0).
+struct MlpConsts {
+  int cf, ncx, ncy;
 };
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,

@@ -487,6 +487,13 @@ __global__ void k_writeback(DevPtrs d) {
     d.prev_other[1][c] = (uint32_t)(d.c_key[c] & 0xFFFFFFFFull);
     d.prev_l0[1][c] = make_float4(L0.x, tw.x, tw.y, tw.z);
     d.prev_l1[1][c] = make_float4(L0.w, L1.x, L1.y, 0.f);
+    if (d.targ) {  // training targets of the learned warm start (final impulses in the slip frame)
+      const float4 sw = d.sdirw[c];
+      const float3 s = f3(sw);
+      d.targ[3 * (size_t)c] = L0.x / sw.w;
+      d.targ[3 * (size_t)c + 1] = dot(tw, s) / sw.w;
+      d.targ[3 * (size_t)c + 2] = dot(tw, cross(n, s)) / sw.w;
+    }
   }
 }
 

@@ -26,7 +26,12 @@ STATIC_BIT = 0x80000000
 EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds_step",
             "tds_synchronize", "tds_read_particles", "tds_read_tool_force", "tds_read_contacts",
             "tds_get_stats", "tds_set_timing", "tds_set_solver", "tds_destroy_scene",
-            "tds_last_error", "tds_find_pair_contacts_noalloc"]
+            "tds_last_error", "tds_find_pair_contacts_noalloc", "tds_mlp_param_count",
+            "tds_set_mlp_weights", "tds_set_recording", "tds_read_training_samples",
+            "tds_mlp_workspace_bytes", "tds_mlp_forward", "tds_mlp_loss_grad", "tds_mlp_adam_step",
+            "tds_set_warm_start"]
+
+WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
 
 class TdsError(RuntimeError):
@@ -98,12 +103,23 @@ def lib() -> ctypes.CDLL:
         L.tds_set_solver.argtypes = [vp, ctypes.c_uint32, ctypes.c_float, ctypes.c_uint32]
         L.tds_find_pair_contacts_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_int32,
                                                      vp, ctypes.c_uint32, vp, vp]
+        L.tds_mlp_param_count.argtypes = []
+        L.tds_set_mlp_weights.argtypes = [vp, vp, ctypes.c_uint32]
+        L.tds_set_recording.argtypes = [vp, ctypes.c_int32]
+        L.tds_set_warm_start.argtypes = [vp, ctypes.c_int32]
+        L.tds_read_training_samples.argtypes = [vp, vp, vp, vp, ctypes.c_uint32,
+                                                ctypes.POINTER(ctypes.c_uint32)]
+        L.tds_mlp_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+        L.tds_mlp_forward.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, vp]
+        L.tds_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, vp, vp]
+        L.tds_mlp_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_float, vp]
         L.tds_destroy_scene.argtypes = [vp]
         L.tds_destroy_scene.restype = None
         L.tds_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("tds_destroy_scene", "tds_last_error"):
                 getattr(L, name).restype = ctypes.c_int32
+        L.tds_mlp_param_count.restype = ctypes.c_uint32
         _lib = L
     return _lib
 
@@ -270,6 +286,31 @@ class Scene:
     def set_timing(self, enable: bool = True):
         _check(lib().tds_set_timing(self.h, int(enable)))
 
+    def set_mlp_weights(self, params: np.ndarray):
+        p = np.ascontiguousarray(np.asarray(params, np.float32).reshape(-1))
+        _check(lib().tds_set_mlp_weights(self.h, ctypes.c_void_p(p.ctypes.data), p.size))
+
+    def set_warm_start(self, mode: int):
+        _check(lib().tds_set_warm_start(self.h, int(mode)))
+
+    def set_recording(self, enable: bool = True):
+        _check(lib().tds_set_recording(self.h, int(enable)))
+
+    def read_training_samples(self) -> dict:
+        """Features (m, 10), targets (m, 3) and keys of the last recorded step,
+        sorted by key."""
+        cnt = ctypes.c_uint32()
+        _check(lib().tds_read_training_samples(self.h, None, None, None, 0, ctypes.byref(cnt)))
+        m = int(cnt.value)
+        feat = np.zeros((m, 10), np.float32)
+        targ = np.zeros((m, 3), np.float32)
+        keys = np.zeros(m, np.uint64)
+        _check(lib().tds_read_training_samples(self.h, ctypes.c_void_p(feat.ctypes.data),
+                                               ctypes.c_void_p(targ.ctypes.data),
+                                               ctypes.c_void_p(keys.ctypes.data), m, ctypes.byref(cnt)))
+        o = np.argsort(keys, kind="stable")
+        return {"features": feat[o], "targets": targ[o], "keys": keys[o]}
+
     def close(self):
         if getattr(self, "h", None):
             lib().tds_destroy_scene(self.h)
@@ -281,3 +322,92 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# the learned warm start's network on device buffers (torch tensors)
+# ---------------------------------------------------------------------------
+PARAM_SHAPES = (("W1", (64, 10)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)),
+                ("W3", (3, 64)), ("b3", (3,)))
+
+
+def param_count() -> int:
+    return int(lib().tds_mlp_param_count())
+
+
+def flatten_params(p: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(p[k], np.float32).reshape(-1) for k, _ in PARAM_SHAPES])
+
+
+def unflatten_params(v) -> dict:
+    v = np.asarray(v, np.float64).reshape(-1)
+    out, o = {}, 0
+    for k, shp in PARAM_SHAPES:
+        sz = int(np.prod(shp))
+        out[k] = v[o:o + sz].reshape(shp)
+        o += sz
+    return out
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-style initial weights (seeded), zero biases."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    p = {"W1": g.normal(0, np.sqrt(2 / 10), (64, 10)), "b1": np.zeros(64),
+         "W2": g.normal(0, np.sqrt(2 / 64), (64, 64)), "b2": np.zeros(64),
+         "W3": g.normal(0, np.sqrt(1 / 64), (3, 64)), "b3": np.zeros(3)}
+    return flatten_params(p)
+
+
+class Net:
+    """FP32 master parameters and Adam moments on the GPU; the forward,
+    loss/gradient and update run in libtds's tensor-core kernels."""
+
+    def __init__(self, params=None, seed: int = 0):
+        import torch
+
+        self.torch = torch
+        p = init_params(seed) if params is None else np.asarray(params, np.float32)
+        self.params = torch.tensor(p, device="cuda")
+        self.grad = torch.zeros_like(self.params)
+        self.mom = torch.zeros_like(self.params)
+        self.vel = torch.zeros_like(self.params)
+        nb = ctypes.c_uint64()
+        _check(lib().tds_mlp_workspace_bytes(ctypes.byref(nb)))
+        self.ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device="cuda")
+        self.loss = torch.zeros(1, device="cuda")
+        self.step_count = 0
+
+    def _ws(self):
+        return ctypes.c_void_p((self.ws.data_ptr() + 255) & ~255)
+
+    def _stream(self):
+        return ctypes.c_void_p(self.torch.cuda.current_stream().cuda_stream)
+
+    def forward(self, X):
+        X = self.torch.as_tensor(X, dtype=self.torch.float32, device="cuda").contiguous()
+        Y = self.torch.empty((X.shape[0], 3), device="cuda")
+        _check(lib().tds_mlp_forward(ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                     X.shape[0], ctypes.c_void_p(Y.data_ptr()), self._ws(), self._stream()))
+        return Y
+
+    def loss_grad(self, X, T):
+        X = self.torch.as_tensor(X, dtype=self.torch.float32, device="cuda").contiguous()
+        T = self.torch.as_tensor(T, dtype=self.torch.float32, device="cuda").contiguous()
+        _check(lib().tds_mlp_loss_grad(ctypes.c_void_p(self.params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                       ctypes.c_void_p(T.data_ptr()), X.shape[0],
+                                       ctypes.c_void_p(self.grad.data_ptr()),
+                                       ctypes.c_void_p(self.loss.data_ptr()), self._ws(), self._stream()))
+        return self.loss, self.grad
+
+    def train_step(self, X, T, lr: float = 1e-3) -> float:
+        self.loss_grad(X, T)
+        self.step_count += 1
+        _check(lib().tds_mlp_adam_step(ctypes.c_void_p(self.params.data_ptr()),
+                                       ctypes.c_void_p(self.grad.data_ptr()),
+                                       ctypes.c_void_p(self.mom.data_ptr()),
+                                       ctypes.c_void_p(self.vel.data_ptr()), self.step_count, float(lr),
+                                       self._stream()))
+        return self.loss
+
+    def host_params(self) -> np.ndarray:
+        return self.params.detach().cpu().numpy().astype(np.float32)
