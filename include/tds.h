@@ -193,6 +193,54 @@ tds_status tds_set_timing(tds_scene *s, int32_t enable);
 
 void tds_destroy_scene(tds_scene *s);
 
+/* ---- batches of independent scenes ------------------------------------------
+ * The paper runs one terrain per simulation; a batch advances several
+ * independent terrain patches (for example the work sites of several
+ * machines, or many training episodes) through the same launches of the
+ * step above. Each scene keeps its own particles, heightfield, walls, tool
+ * and friction coefficients (mu_t, mu_r, mu_tool); all scenes share dt,
+ * gravity, density, young, poisson, cohesion, the solver settings,
+ * warm_start and contacts_per_particle (creation fails otherwise). Scenes
+ * never interact: every scene of a batch steps exactly as it would alone.
+ * A batch is a tds_scene handle; the calls above apply to it as a whole:
+ * particle ids are global, scene q owning ids [o_q, o_q + n_q) with o_q the
+ * sum of the earlier scenes' n; tds_set_tool_pose and tds_read_tool_force
+ * address scene 0; statistics are summed over the batch (one solve: the
+ * sweep count and residual are the batch's). tds_create_scene is a batch of
+ * one. */
+tds_status tds_batch_workspace_bytes(const tds_scene_desc *descs, uint32_t count, uint64_t *bytes);
+tds_status tds_create_batch(const tds_scene_desc *descs, uint32_t count, void *workspace,
+                            uint64_t workspace_bytes, void *stream, tds_scene **out);
+
+/* Tool pose of scene `scene` of the batch (as tds_set_tool_pose). */
+tds_status tds_batch_set_tool_pose(tds_scene *s, uint32_t scene, const float pos[3],
+                                   const float quat[4], const float linvel[3],
+                                   const float angvel[3]);
+
+/* Tool poses of all scenes in one call: 13 floats per scene (position 3,
+ * quaternion w,x,y,z 4, linear velocity 3, angular velocity 3), count = the
+ * number of scenes. Stops at the first invalid pose (earlier scenes keep
+ * their new pose). */
+tds_status tds_batch_set_tool_poses(tds_scene *s, const float *poses, uint32_t count);
+
+/* Particle state of scene `scene` (n must equal its particle count; arrays
+ * indexed by the scene-local id). Waits. */
+tds_status tds_batch_read_particles(tds_scene *s, uint32_t scene, float *x, float *y, float *z,
+                                    float *vx, float *vy, float *vz, float *wx, float *wy,
+                                    float *wz, uint32_t n);
+
+/* Force and torque on every scene's tool during the last step: 6 floats per
+ * scene (fx, fy, fz, tx, ty, tz), count = the number of scenes. Waits. */
+tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_t count);
+
+/* Replay each step from a CUDA graph (1) or launch its kernels one by one
+ * (0, the default). The graph is captured on the next step and captured
+ * again whenever the warm start, recording or solver settings change; tool
+ * poses need no capture. Results are identical either way. Needs a stream
+ * created by the caller (not the legacy default stream). With graphs on,
+ * per-phase timing reports the whole step as its first phase. */
+tds_status tds_set_graph(tds_scene *s, int32_t enable);
+
 /* ---- learned warm start ------------------------------------------------------
  * Not in the paper, whose discussion proposes data-driven models trained on
  * resolved simulations as future work: a 10 -> 64 -> 64 -> 3 ReLU network

@@ -1,6 +1,7 @@
-// tds_api.cu -- host side of the C ABI declared in include/tds.h: scene
-// creation and workspace layout, per-step orchestration of the kernels on the
-// scene's stream, and the read calls.
+// tds_api.cu -- host side of the C ABI declared in include/tds.h: scene and
+// batch creation with the workspace layout, per-scene geometry tables, the
+// per-step orchestration of the kernels on the scene's stream (optionally
+// replayed as CUDA graphs), and the read calls. A scene is a batch of one.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -9,14 +10,14 @@
 
 #include "tds_internal.cuh"
 
-// launchers (tds_contacts.cu, tds_colour.cu, tds_solve.cu)
+// launchers (tds_contacts.cu, tds_colour.cu, tds_solve.cu, tds_mlp.cu)
 int tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st);
 int tds_launch_narrowphase(const DevPtrs &d, const StepConsts &k, int use_prev, cudaStream_t st);
 int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_blocks,
                          int coop_threads, cudaStream_t st);
 int tds_launch_bucketing(const DevPtrs &d, uint32_t cap, cudaStream_t st);
-void tds_launch_features(const DevPtrs &d, const StepConsts &k, const MlpConsts &q, int *surf,
-                         uint32_t cap, cudaStream_t st);
+int tds_launch_features(const DevPtrs &d, const StepConsts &k, int *surf, uint32_t ncols, uint32_t cap,
+                        cudaStream_t st);
 void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, cudaStream_t st);
 size_t tds_mlp_packed_bytes();
 int tds_mlp_params();
@@ -81,35 +82,62 @@ struct Carver {
   }
 };
 
-struct Sizes {
-  uint32_t n, cap, ncells, ntiles, hf_words;
-  int gnx, gny, gnz;
-  float lo[3], cell;
-  MlpConsts mq;  // surface columns of the learned warm start
+// Per-scene host data of a batch.
+struct SceneHost {
+  uint32_t off, n;                  // particle ids [off, off + n)
+  std::vector<float> walls, tools;  // 10 floats per box
+  float pos[3] = {0, 0, 0}, quat[4] = {1, 0, 0, 0}, vel[3] = {0, 0, 0}, angvel[3] = {0, 0, 0};
+};
+
+struct Layout {
+  uint32_t S = 0, n = 0, cap = 0, ncells = 0, ntiles = 0, nheights = 1, nboxes = 0, ncols = 0;
+  int gnx = 1, gny = 1, gnz = 1;
+  float cell = 1.f;
+  std::vector<SceneGeo> geo;
 };
 
 struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
-  float *hf = nullptr;
+  float *heights = nullptr;
+  SceneGeo *geo = nullptr;
+  BoxF *boxes = nullptr;
   int *surf = nullptr;
   void *packed = nullptr;
   float *params = nullptr;
   float *targ = nullptr;
 };
 
+// What a captured step depends on besides device memory: the kernel
+// arguments that the host settings select.
+struct GraphKey {
+  int use_prev = -1, warm = -1, recording = -1;
+  uint32_t max_iters = 0, every = 0;
+  float tol = -1.f;
+  bool operator==(const GraphKey &o) const {
+    return use_prev == o.use_prev && warm == o.warm && recording == o.recording &&
+           max_iters == o.max_iters && every == o.every && tol == o.tol;
+  }
+};
+
+struct StepGraph {  // a captured step for one parity of the double buffers
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key;
+  uint64_t launches = 0;
+};
+
 }  // namespace
 
 struct tds_scene {
-  tds_scene_desc desc;
-  Sizes sz;
+  tds_scene_desc desc;  // the common settings (solver, material, step)
+  Layout L;
   StepConsts k;
   DevPtrs d;
   cudaStream_t st = nullptr;
   void *mem = nullptr;
   bool owns = false;
   bool have_prev = false;
-  std::vector<float> walls, tool_boxes;
-  float tool_pos[3] = {0, 0, 0}, tool_quat[4] = {1, 0, 0, 0}, tool_vel[3] = {0, 0, 0},
-        tool_angvel[3] = {0, 0, 0};
+  std::vector<SceneHost> scenes;
+  std::vector<BoxF> host_boxes;
+  bool geo_dirty = true;
   int pgs_blocks = 1, colour_blocks = 1;
   uint64_t steps = 0;
   tds_status latched = TDS_OK;
@@ -119,6 +147,9 @@ struct tds_scene {
   size_t ev_used = 0;
   Extra x;
   bool recording = false, have_weights = false;
+  bool graph = false;
+  StepGraph graphs[2];
+  uint32_t parity = 0;
 };
 
 namespace {
@@ -148,86 +179,142 @@ tds_status validate(const tds_scene_desc *d) {
   return TDS_OK;
 }
 
-Sizes plan(const tds_scene_desc *d) {
-  Sizes s{};
-  s.n = d->n;
-  uint32_t per = d->contacts_per_particle ? d->contacts_per_particle : 10u;
-  uint64_t cap = (uint64_t)per * d->n + 64;
-  if (cap > 0x7FFFFFF0ull) cap = 0x7FFFFFF0ull;
-  s.cap = (uint32_t)cap;
-  s.ntiles = (s.cap + TDS_TILE - 1) / TDS_TILE;
-  float rmax = 0.f;
-  for (uint32_t i = 0; i < d->n; ++i) rmax = std::fmax(rmax, d->radius[i]);
-  // cell wider than any reach (2 rmax plus the cohesive band), with margin
-  s.cell = 2.0f * rmax * 1.025f * 1.02f;
-  float lo[3], hi[3];
+// Scenes of one batch share the step, material and solver settings.
+tds_status validate_batch(const tds_scene_desc *descs, uint32_t count) {
+  if (!descs || count == 0) return fail(TDS_ERR_INVALID_ARG, "descs is NULL or count is 0");
+  uint64_t total = 0;
+  for (uint32_t s = 0; s < count; ++s) {
+    tds_status v = validate(descs + s);
+    if (v != TDS_OK) return v;
+    total += descs[s].n;
+    const tds_scene_desc &a = descs[0], &b = descs[s];
+    if (a.dt != b.dt || a.gravity[0] != b.gravity[0] || a.gravity[1] != b.gravity[1] ||
+        a.gravity[2] != b.gravity[2] || a.density != b.density || a.young != b.young ||
+        a.poisson != b.poisson || a.cohesion != b.cohesion || a.max_iters != b.max_iters ||
+        a.tol != b.tol || a.residual_every != b.residual_every || a.warm_start != b.warm_start ||
+        a.contacts_per_particle != b.contacts_per_particle)
+      return fail(TDS_ERR_INVALID_ARG,
+                  "scenes of a batch must share dt, gravity, density, young, poisson, cohesion, the "
+                  "solver settings, warm_start and contacts_per_particle");
+  }
+  if (total >= 0x7FFFFFFFull) return fail(TDS_ERR_INVALID_ARG, "too many particles in the batch");
+  return TDS_OK;
+}
+
+// Broadphase domain of one scene: the given box, or its particles and walls
+// with a margin and headroom above.
+void scene_domain(const tds_scene_desc *d, float cell, float lo[3], float hi[3]) {
   bool given = false;
   for (int a = 0; a < 3; ++a) given |= d->domain_hi[a] > d->domain_lo[a];
   if (given) {
     for (int a = 0; a < 3; ++a) { lo[a] = d->domain_lo[a]; hi[a] = d->domain_hi[a]; }
-  } else {
-    const float *xs[3] = {d->x, d->y, d->z};
-    for (int a = 0; a < 3; ++a) {
-      lo[a] = hi[a] = xs[a][0];
-      for (uint32_t i = 1; i < d->n; ++i) {
-        lo[a] = std::fmin(lo[a], xs[a][i]);
-        hi[a] = std::fmax(hi[a], xs[a][i]);
-      }
-    }
-    for (uint32_t w = 0; w < d->n_walls; ++w) {  // inner faces of the walls bound the bed
-      const float *b = d->walls + 10 * w;
-      double R[9];
-      quat_to_matrix(b + 3, R);
-      for (int a = 0; a < 3; ++a) {
-        double ext = std::fabs(R[3 * a]) * b[7] + std::fabs(R[3 * a + 1]) * b[8] + std::fabs(R[3 * a + 2]) * b[9];
-        if (a < 2) {
-          lo[a] = std::fmin(lo[a], (float)(b[a] - ext));
-          hi[a] = std::fmax(hi[a], (float)(b[a] + ext));
-        }
-      }
-    }
-    float margin = 2.0f * s.cell;
-    for (int a = 0; a < 3; ++a) { lo[a] -= margin; hi[a] += margin; }
-    hi[2] += 0.25f * (hi[2] - lo[2]);
+    return;
   }
-  int dims[3];
-  for (;;) {
-    uint64_t tot = 1;
-    for (int a = 0; a < 3; ++a) {
-      dims[a] = (int)std::ceil((hi[a] - lo[a]) / s.cell);
-      if (dims[a] < 1) dims[a] = 1;
-      tot *= (uint64_t)dims[a];
+  const float *xs[3] = {d->x, d->y, d->z};
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = hi[a] = xs[a][0];
+    for (uint32_t i = 1; i < d->n; ++i) {
+      lo[a] = std::fmin(lo[a], xs[a][i]);
+      hi[a] = std::fmax(hi[a], xs[a][i]);
     }
-    if (tot <= (1ull << 26)) break;
-    s.cell *= 1.25f;  // coarser cells keep the grid bounded; correctness is unaffected
   }
-  s.gnx = dims[0]; s.gny = dims[1]; s.gnz = dims[2];
-  s.ncells = (uint32_t)((uint64_t)dims[0] * dims[1] * dims[2]);
-  for (int a = 0; a < 3; ++a) s.lo[a] = lo[a];
-  s.hf_words = d->hf_nx > 0 ? (d->hf_nx + 1) * (d->hf_ny + 1) : 1;
-  // surface columns: heightfield cells grouped cf x cf, cf the smallest
-  // integer with cf * cell >= 4 r_max
-  s.mq = MlpConsts{0, 1, 1};
-  if (d->hf_nx > 0) {
-    int cf = (int)std::ceil(4.0 * (double)rmax / (double)d->hf_cell);
-    if (cf < 1) cf = 1;
-    s.mq.cf = cf;
-    s.mq.ncx = ((int)d->hf_nx + cf - 1) / cf;
-    s.mq.ncy = ((int)d->hf_ny + cf - 1) / cf;
+  for (uint32_t w = 0; w < d->n_walls; ++w) {  // the walls bound the bed
+    const float *b = d->walls + 10 * w;
+    double R[9];
+    quat_to_matrix(b + 3, R);
+    for (int a = 0; a < 2; ++a) {
+      double ext = std::fabs(R[3 * a]) * b[7] + std::fabs(R[3 * a + 1]) * b[8] + std::fabs(R[3 * a + 2]) * b[9];
+      lo[a] = std::fmin(lo[a], (float)(b[a] - ext));
+      hi[a] = std::fmax(hi[a], (float)(b[a] + ext));
+    }
   }
-  return s;
+  float margin = 2.0f * cell;
+  for (int a = 0; a < 3; ++a) { lo[a] -= margin; hi[a] += margin; }
+  hi[2] += 0.25f * (hi[2] - lo[2]);
 }
 
-size_t carve(Carver &c, const Sizes &s, DevPtrs &d, Extra &x, int pgs_blocks) {
-  const uint32_t n = s.n, cap = s.cap;
+Layout plan(const tds_scene_desc *descs, uint32_t S) {
+  Layout L;
+  L.S = S;
+  uint64_t cap = 64;
+  uint32_t per = descs[0].contacts_per_particle ? descs[0].contacts_per_particle : 10u;
+  float rmax = 0.f;
+  for (uint32_t s = 0; s < S; ++s) {
+    L.n += descs[s].n;
+    cap += (uint64_t)per * descs[s].n;
+    for (uint32_t i = 0; i < descs[s].n; ++i) rmax = std::fmax(rmax, descs[s].radius[i]);
+  }
+  if (cap > 0x7FFFFFF0ull) cap = 0x7FFFFFF0ull;
+  L.cap = (uint32_t)cap;
+  L.ntiles = (L.cap + TDS_TILE - 1) / TDS_TILE;
+  // cells wider than any reach (2 r_max plus the cohesive band), with margin
+  L.cell = 2.0f * rmax * 1.025f * 1.02f;
+  std::vector<float> lo(3 * S), hi(3 * S);
+  for (;;) {
+    int dims[3] = {1, 1, 1};
+    for (uint32_t s = 0; s < S; ++s) {
+      scene_domain(descs + s, L.cell, &lo[3 * s], &hi[3 * s]);
+      for (int a = 0; a < 3; ++a) {
+        int n = (int)std::ceil((hi[3 * s + a] - lo[3 * s + a]) / L.cell);
+        dims[a] = std::max(dims[a], std::max(n, 1));
+      }
+    }
+    uint64_t tot = (uint64_t)S * dims[0] * dims[1] * dims[2];
+    if (tot <= (1ull << 26)) {
+      L.gnx = dims[0]; L.gny = dims[1]; L.gnz = dims[2];
+      L.ncells = (uint32_t)tot;
+      break;
+    }
+    L.cell *= 1.25f;  // coarser cells keep the grid bounded; correctness is unaffected
+  }
+  L.geo.resize(S);
+  uint32_t hoff = 0, boff = 0, coff = 0, pid0 = 0;
+  for (uint32_t s = 0; s < S; ++s) {
+    const tds_scene_desc &d = descs[s];
+    SceneGeo &G = L.geo[s];
+    std::memset(&G, 0, sizeof(G));
+    for (int a = 0; a < 3; ++a) G.lo[a] = lo[3 * s + a];
+    G.hf_nx = (int)d.hf_nx; G.hf_ny = (int)d.hf_ny;
+    G.hf_x0 = d.hf_x0; G.hf_y0 = d.hf_y0; G.hf_cell = d.hf_cell;
+    G.hf_off = hoff;
+    if (d.hf_nx > 0) hoff += (d.hf_nx + 1) * (d.hf_ny + 1);
+    G.box0 = boff;
+    G.nbox = d.n_walls + d.n_tool_boxes;
+    G.nwall = d.n_walls;
+    boff += G.nbox;
+    G.mu_t = d.mu_t; G.mu_tool = d.mu_tool; G.mu_r = d.mu_r;
+    G.pid0 = pid0;
+    pid0 += d.n;
+    // surface columns of the learned warm start: heightfield cells grouped
+    // cf x cf, cf the smallest integer with cf * cell >= 4 r_max of the scene
+    if (d.hf_nx > 0) {
+      float rs = 0.f;
+      for (uint32_t i = 0; i < d.n; ++i) rs = std::fmax(rs, d.radius[i]);
+      int cf = (int)std::ceil(4.0 * (double)rs / (double)d.hf_cell);
+      if (cf < 1) cf = 1;
+      G.cf = cf;
+      G.ncx = ((int)d.hf_nx + cf - 1) / cf;
+      G.ncy = ((int)d.hf_ny + cf - 1) / cf;
+      G.col_off = coff;
+      coff += (uint32_t)(G.ncx * G.ncy);
+    }
+  }
+  L.nheights = hoff ? hoff : 1;
+  L.nboxes = boff;
+  L.ncols = coff;
+  return L;
+}
+
+size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
+  const uint32_t n = L.n, cap = L.cap;
   d.pos = c.take<float4>(n); d.pv = c.take<float4>(2 * (size_t)n);
-  d.pid = c.take<uint32_t>(n);
+  d.pid = c.take<uint32_t>(n); d.sid = c.take<uint32_t>(n);
   d.pos2 = c.take<float4>(n); d.pv2 = c.take<float4>(2 * (size_t)n);
-  d.pid2 = c.take<uint32_t>(n);
+  d.pid2 = c.take<uint32_t>(n); d.sid2 = c.take<uint32_t>(n);
   d.cell_of = c.take<uint32_t>(n);
-  d.cell_count = c.take<uint32_t>(s.ncells + 1);
-  d.cell_start = c.take<uint32_t>(s.ncells + 1);
-  d.cell_cursor = c.take<uint32_t>(s.ncells);
+  d.cell_count = c.take<uint32_t>(L.ncells + 1);
+  d.cell_start = c.take<uint32_t>(L.ncells + 1);
+  d.cell_cursor = c.take<uint32_t>(L.ncells);
   d.perm = c.take<uint32_t>(n);
   d.cnt = c.take<uint32_t>(n + 1);
   d.cstart = c.take<uint32_t>(n + 1);
@@ -243,9 +330,9 @@ size_t carve(Carver &c, const Sizes &s, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.colour = c.take<uint8_t>(cap);
   d.wait = c.take<int32_t>(cap);
   d.frontier0 = c.take<uint32_t>(cap); d.frontier1 = c.take<uint32_t>(cap);
-  d.ntiles = s.ntiles;
-  d.tile_hist = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles);
-  d.tile_off = c.take<uint32_t>((size_t)TDS_NBUCKETS * s.ntiles + 1);
+  d.ntiles = L.ntiles;
+  d.tile_hist = c.take<uint32_t>((size_t)TDS_NBUCKETS * L.ntiles);
+  d.tile_off = c.take<uint32_t>((size_t)TDS_NBUCKETS * L.ntiles + 1);
   d.bstart = c.take<uint32_t>(TDS_NBUCKETS + 1);
   d.bend = c.take<uint32_t>(TDS_NBUCKETS);
   d.bpad = c.take<uint32_t>(TDS_NBUCKETS);
@@ -271,20 +358,23 @@ size_t carve(Carver &c, const Sizes &s, DevPtrs &d, Extra &x, int pgs_blocks) {
   if (nd < 6 * 128) nd = 6 * 128;
   d.dpart = c.take<double>(nd);
   d.bar = c.take<uint32_t>(2);
-  size_t m = s.ncells;
+  size_t m = L.ncells;
   if (m < n) m = n;
-  if (m < (size_t)TDS_NBUCKETS * s.ntiles) m = (size_t)TDS_NBUCKETS * s.ntiles;
+  if (m < (size_t)TDS_NBUCKETS * L.ntiles) m = (size_t)TDS_NBUCKETS * L.ntiles;
   d.scan_tmp = c.take<uint32_t>(tds_scan_tmp_words((uint32_t)m));
   d.stage = c.take<float>(9 * (size_t)n);
-  d.tool_out = c.take<float>(6);
+  d.tool_out = c.take<float>(6 * (size_t)L.S);
+  d.tool_acc = c.take<double>(6 * (size_t)L.S);
   d.feat = c.take<float>(10 * (size_t)cap);
   d.sdirw = c.take<float4>(cap);
   d.c_flag = c.take<uint8_t>(cap);
   x.targ = c.take<float>(3 * (size_t)cap);
-  x.surf = c.take<int>((size_t)s.mq.ncx * s.mq.ncy);
+  x.surf = c.take<int>(L.ncols);
   x.packed = c.take<unsigned char>(tds_mlp_packed_bytes());
   x.params = c.take<float>(tds_mlp_params());
-  x.hf = c.take<float>(s.hf_words);
+  x.heights = c.take<float>(L.nheights);
+  x.geo = c.take<SceneGeo>(L.S);
+  x.boxes = c.take<BoxF>(L.nboxes);
   return c.off + 256;
 }
 
@@ -300,38 +390,41 @@ void set_box(BoxF &B, const double R[9], const double c[3], const float h[3], in
   B.is_tool = is_tool;
 }
 
-// World-frame boxes for the current tool pose: walls as given, tool boxes
-// composed as R_w = R_T R_k, c_w = p_T + R_T c_k in FP64, then rounded.
-void compose_boxes(tds_scene *s) {
-  StepConsts &k = s->k;
-  k.n_walls = (int)s->desc.n_walls;
-  k.nb = (int)(s->desc.n_walls + s->desc.n_tool_boxes);
-  for (uint32_t w = 0; w < s->desc.n_walls; ++w) {
-    const float *b = s->walls.data() + 10 * w;
+// World-frame boxes of scene s for its current tool pose: walls as given,
+// tool boxes composed as R_w = R_T R_k, c_w = p_T + R_T c_k in FP64, then
+// rounded; the tool motion goes to the scene's table entry.
+void compose_boxes(tds_scene *S, uint32_t s) {
+  const SceneHost &h = S->scenes[s];
+  SceneGeo &G = S->L.geo[s];
+  BoxF *out = S->host_boxes.data() + G.box0;
+  const uint32_t nw = G.nwall, nt = G.nbox - G.nwall;
+  for (uint32_t w = 0; w < nw; ++w) {
+    const float *b = h.walls.data() + 10 * w;
     double R[9], c[3] = {b[0], b[1], b[2]};
     quat_to_matrix(b + 3, R);
-    set_box(k.box[w], R, c, b + 7, 0);
+    set_box(out[w], R, c, b + 7, 0);
   }
   double RT[9];
-  quat_to_matrix(s->tool_quat, RT);
-  for (uint32_t t = 0; t < s->desc.n_tool_boxes; ++t) {
-    const float *b = s->tool_boxes.data() + 10 * t;
+  quat_to_matrix(h.quat, RT);
+  for (uint32_t t = 0; t < nt; ++t) {
+    const float *b = h.tools.data() + 10 * t;
     double Rk[9], Rw[9], c[3];
     quat_to_matrix(b + 3, Rk);
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
         Rw[3 * i + j] = (RT[3 * i + 0] * Rk[0 + j] + RT[3 * i + 1] * Rk[3 + j]) + RT[3 * i + 2] * Rk[6 + j];
     for (int i = 0; i < 3; ++i) {
-      double off = (RT[3 * i + 0] * (double)b[0] + RT[3 * i + 1] * (double)b[1]) + RT[3 * i + 2] * (double)b[2];
-      c[i] = (double)s->tool_pos[i] + off;
+      double o = (RT[3 * i + 0] * (double)b[0] + RT[3 * i + 1] * (double)b[1]) + RT[3 * i + 2] * (double)b[2];
+      c[i] = (double)h.pos[i] + o;
     }
-    set_box(k.box[s->desc.n_walls + t], Rw, c, b + 7, 1);
+    set_box(out[nw + t], Rw, c, b + 7, 1);
   }
   for (int i = 0; i < 3; ++i) {
-    k.tp[i] = s->tool_pos[i];
-    k.tv[i] = s->tool_vel[i];
-    k.tw[i] = s->tool_angvel[i];
+    G.tp[i] = h.pos[i];
+    G.tv[i] = h.vel[i];
+    G.tw[i] = h.angvel[i];
   }
+  S->geo_dirty = true;
 }
 
 tds_status check_latched(tds_scene *s) {
@@ -359,43 +452,43 @@ tds_status sync_and_check(tds_scene *s) {
   return TDS_OK;
 }
 
-}  // namespace
-
-// Lets other translation units of the library report through tds_last_error.
-tds_status tds_set_error_message(tds_status s, const char *msg) { return fail(s, msg); }
-
-extern "C" {
-
-const char *tds_last_error(void) { return g_err.c_str(); }
-
-tds_status tds_workspace_bytes(const tds_scene_desc *desc, uint64_t *bytes) {
-  tds_status v = validate(desc);
+tds_status workspace_bytes_impl(const tds_scene_desc *descs, uint32_t count, uint64_t *bytes) {
+  tds_status v = validate_batch(descs, count);
   if (v != TDS_OK) return v;
   if (!bytes) return fail(TDS_ERR_INVALID_ARG, "bytes is NULL");
-  Sizes s = plan(desc);
+  Layout L = plan(descs, count);
   DevPtrs d{};
   Extra x;
   Carver c{nullptr};
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  *bytes = carve(c, s, d, x, 64 * sms);
+  *bytes = carve(c, L, d, x, 64 * sms);
   return TDS_OK;
 }
 
-tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_t workspace_bytes,
-                            void *stream, tds_scene **out) {
-  tds_status v = validate(desc);
+tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *workspace, uint64_t workspace_bytes,
+                       void *stream, tds_scene **out) {
+  tds_status v = validate_batch(descs, count);
   if (v != TDS_OK) return v;
   if (!out) return fail(TDS_ERR_INVALID_ARG, "out is NULL");
   if (workspace && ((uintptr_t)workspace & 255u))
     return fail(TDS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
   *out = nullptr;
   tds_scene *s = new tds_scene();
-  s->desc = *desc;
+  s->desc = descs[0];
   s->st = (cudaStream_t)stream;
-  s->sz = plan(desc);
-  if (desc->n_walls) s->walls.assign(desc->walls, desc->walls + 10 * desc->n_walls);
-  if (desc->n_tool_boxes) s->tool_boxes.assign(desc->tool_boxes, desc->tool_boxes + 10 * desc->n_tool_boxes);
+  s->L = plan(descs, count);
+  s->scenes.resize(count);
+  uint32_t off = 0;
+  for (uint32_t q = 0; q < count; ++q) {
+    SceneHost &h = s->scenes[q];
+    h.off = off;
+    h.n = descs[q].n;
+    off += h.n;
+    if (descs[q].n_walls) h.walls.assign(descs[q].walls, descs[q].walls + 10 * descs[q].n_walls);
+    if (descs[q].n_tool_boxes)
+      h.tools.assign(descs[q].tool_boxes, descs[q].tool_boxes + 10 * descs[q].n_tool_boxes);
+  }
   int dev = 0, sms = 0, occ_pgs = 0, occ_col = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -406,12 +499,12 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
     delete s;
     return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
   }
-  s->pgs_blocks = pgs_blocks_for(desc->n, sms);  // one co-resident CTA per SM at most
+  s->pgs_blocks = pgs_blocks_for(s->L.n, sms);  // one co-resident CTA per SM at most
   s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
   Carver probe{nullptr};
   DevPtrs tmp{};
   Extra tx;
-  size_t need = carve(probe, s->sz, tmp, tx, 64 * sms);
+  size_t need = carve(probe, s->L, tmp, tx, 64 * sms);
   if (workspace) {
     if (workspace_bytes < need) {
       delete s;
@@ -427,88 +520,259 @@ tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_
     s->owns = true;
   }
   Carver c{(char *)s->mem};
-  carve(c, s->sz, s->d, s->x, 64 * sms);
-  float *hf = s->x.hf;
+  carve(c, s->L, s->d, s->x, 64 * sms);
   s->d.targ = nullptr;
-  // constants
+  // common constants
+  const tds_scene_desc &D = descs[0];
   StepConsts &k = s->k;
   std::memset(&k, 0, sizeof(k));
-  k.n = desc->n;
-  k.cap = s->sz.cap;
-  k.dt = desc->dt;
-  for (int i = 0; i < 3; ++i) k.g[i] = desc->gravity[i];
-  k.ups = 1.0f / (1.0f + 4.0f * (2.0f * desc->dt) / desc->dt);
-  double nu = desc->poisson, E = desc->young;
+  k.n = s->L.n;
+  k.cap = s->L.cap;
+  k.nscenes = count;
+  k.dt = D.dt;
+  for (int i = 0; i < 3; ++i) k.g[i] = D.gravity[i];
+  k.ups = 1.0f / (1.0f + 4.0f * (2.0f * D.dt) / D.dt);
+  double nu = D.poisson, E = D.young;
   k.estar_pair = (float)(1.0 / (2.0 * (1.0 - nu * nu) / E));
   k.estar_static = (float)(E / (1.0 - nu * nu));
-  k.mu_t = desc->mu_t; k.mu_tool = desc->mu_tool; k.mu_r = desc->mu_r;
-  k.cohesion = desc->cohesion;
-  k.cohesive = desc->cohesion > 0.f;
-  k.sig_t = 1e-9f / desc->dt;
-  k.sig_r = 1e-9f / desc->dt;
-  k.gx0 = s->sz.lo[0]; k.gy0 = s->sz.lo[1]; k.gz0 = s->sz.lo[2];
-  k.cell_inv = 1.0f / s->sz.cell;
-  k.gnx = s->sz.gnx; k.gny = s->sz.gny; k.gnz = s->sz.gnz;
-  k.hf_nx = (int)desc->hf_nx; k.hf_ny = (int)desc->hf_ny;
-  k.hf_x0 = desc->hf_x0; k.hf_y0 = desc->hf_y0; k.hf_cell = desc->hf_cell;
-  k.hf_h = hf;
-  compose_boxes(s);
-  // upload particle state: (x, r), (v, 1/m), (w, 1/I), ids
-  const uint32_t n = desc->n;
+  k.cohesion = D.cohesion;
+  k.cohesive = D.cohesion > 0.f;
+  k.sig_t = 1e-9f / D.dt;
+  k.sig_r = 1e-9f / D.dt;
+  k.cell_inv = 1.0f / s->L.cell;
+  k.gnx = s->L.gnx; k.gny = s->L.gny; k.gnz = s->L.gnz;
+  k.geo = s->x.geo;
+  k.boxes = s->x.boxes;
+  k.heights = s->x.heights;
+  s->host_boxes.resize(s->L.nboxes);
+  for (uint32_t q = 0; q < count; ++q) compose_boxes(s, q);
+  // particle state: (x, r), (v, 1/m | w, 1/I), ids, scenes
+  const uint32_t n = s->L.n;
   std::vector<float4> P(n), PV(2 * (size_t)n);
-  std::vector<uint32_t> ids(n);
+  std::vector<uint32_t> ids(n), sids(n);
+  std::vector<float> heights(s->L.nheights, 0.f);
   const double pi = 3.14159265358979323846;
-  for (uint32_t i = 0; i < n; ++i) {
-    double r = desc->radius[i];
-    double m = desc->density * 4.0 / 3.0 * pi * r * r * r;
-    double I = 0.4 * m * r * r;
-    P[i] = make_float4(desc->x[i], desc->y[i], desc->z[i], desc->radius[i]);
-    PV[2 * i] = make_float4(desc->vx ? desc->vx[i] : 0.f, desc->vy ? desc->vy[i] : 0.f,
-                            desc->vz ? desc->vz[i] : 0.f, (float)(1.0 / m));
-    PV[2 * i + 1] = make_float4(desc->wx ? desc->wx[i] : 0.f, desc->wy ? desc->wy[i] : 0.f,
-                                desc->wz ? desc->wz[i] : 0.f, (float)(1.0 / I));
-    ids[i] = i;
+  for (uint32_t q = 0; q < count; ++q) {
+    const tds_scene_desc &d = descs[q];
+    const uint32_t o = s->scenes[q].off;
+    for (uint32_t i = 0; i < d.n; ++i) {
+      double r = d.radius[i];
+      double m = d.density * 4.0 / 3.0 * pi * r * r * r;
+      double I = 0.4 * m * r * r;
+      P[o + i] = make_float4(d.x[i], d.y[i], d.z[i], d.radius[i]);
+      PV[2 * (size_t)(o + i)] = make_float4(d.vx ? d.vx[i] : 0.f, d.vy ? d.vy[i] : 0.f, d.vz ? d.vz[i] : 0.f,
+                                            (float)(1.0 / m));
+      PV[2 * (size_t)(o + i) + 1] = make_float4(d.wx ? d.wx[i] : 0.f, d.wy ? d.wy[i] : 0.f,
+                                                d.wz ? d.wz[i] : 0.f, (float)(1.0 / I));
+      ids[o + i] = o + i;
+      sids[o + i] = q;
+    }
+    if (d.hf_nx > 0)
+      std::memcpy(heights.data() + s->L.geo[q].hf_off, d.hf_heights,
+                  sizeof(float) * (d.hf_nx + 1) * (d.hf_ny + 1));
   }
-  auto cleanup_fail = [&](const std::string &msg) {
-    if (s->owns) cudaFree(s->mem);
-    delete s;
-    return fail(TDS_ERR_CUDA, msg);
-  };
   if (cudaMemcpyAsync(s->d.pos, P.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.pv, PV.data(), sizeof(float4) * 2 * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.pid, ids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
-      (desc->hf_nx > 0 &&
-       cudaMemcpyAsync(hf, desc->hf_heights, sizeof(float) * s->sz.hf_words, cudaMemcpyHostToDevice, s->st)) ||
+      cudaMemcpyAsync(s->d.sid, sids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
+      cudaMemcpyAsync(s->x.heights, heights.data(), sizeof(float) * heights.size(), cudaMemcpyHostToDevice,
+                      s->st) ||
       cudaMemsetAsync(s->d.err, 0, sizeof(int32_t), s->st) ||
       cudaMemsetAsync(s->d.ctr, 0, sizeof(uint32_t) * CTR_COUNT, s->st) ||
       cudaMemsetAsync(s->d.acc, 0, sizeof(unsigned long long) * ACC_COUNT, s->st) ||
       cudaMemsetAsync(s->d.fscal, 0, sizeof(float) * FS_COUNT, s->st) ||
-      cudaMemsetAsync(s->d.tool_out, 0, sizeof(float) * 6, s->st) ||
+      cudaMemsetAsync(s->d.tool_out, 0, sizeof(float) * 6 * count, s->st) ||
+      cudaMemsetAsync(s->d.tool_acc, 0, sizeof(double) * 6 * count, s->st) ||
       cudaMemsetAsync(s->d.bstart, 0, sizeof(uint32_t) * (TDS_NBUCKETS + 1), s->st) ||
       cudaMemsetAsync(s->d.bend, 0, sizeof(uint32_t) * TDS_NBUCKETS, s->st) ||
       cudaStreamSynchronize(s->st)) {
     cudaGetLastError();
-    return cleanup_fail("uploading the scene failed");
+    if (s->owns) cudaFree(s->mem);
+    delete s;
+    return fail(TDS_ERR_CUDA, "uploading the scene failed");
   }
   *out = s;
   return TDS_OK;
 }
 
-tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[4],
-                             const float linvel[3], const float angvel[3]) {
+tds_status set_pose_impl(tds_scene *s, uint32_t q, const float pos[3], const float quat[4],
+                         const float linvel[3], const float angvel[3]) {
   if (!s || !pos || !quat || !linvel || !angvel) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (q >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "scene index out of range");
   double qn = std::sqrt((double)quat[0] * quat[0] + (double)quat[1] * quat[1] +
                         (double)quat[2] * quat[2] + (double)quat[3] * quat[3]);
   if (!(qn > 1e-6)) return fail(TDS_ERR_INVALID_ARG, "quaternion has zero norm");
+  SceneHost &h = s->scenes[q];
   for (int i = 0; i < 3; ++i) {
     if (!std::isfinite(pos[i]) || !std::isfinite(linvel[i]) || !std::isfinite(angvel[i]))
       return fail(TDS_ERR_INVALID_ARG, "non-finite tool pose");
-    s->tool_pos[i] = pos[i];
-    s->tool_vel[i] = linvel[i];
-    s->tool_angvel[i] = angvel[i];
+    h.pos[i] = pos[i];
+    h.vel[i] = linvel[i];
+    h.angvel[i] = angvel[i];
   }
-  for (int i = 0; i < 4; ++i) s->tool_quat[i] = quat[i];
-  compose_boxes(s);
+  for (int i = 0; i < 4; ++i) h.quat[i] = quat[i];
+  compose_boxes(s, q);
+  return TDS_OK;
+}
+
+// The kernels of one step, in order, on the scene's stream (capturable).
+tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches) {
+  DevPtrs &d = s->d;
+  const tds_scene_desc &D = s->desc;
+  if (E) CUDA_TRY(cudaEventRecord(E[0], s->st));
+  launches += tds_launch_broadphase(d, s->k, s->L.ncells, s->st);
+  std::swap(d.pos, d.pos2);
+  std::swap(d.pv, d.pv2);
+  std::swap(d.pid, d.pid2);
+  std::swap(d.sid, d.sid2);
+  if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
+  const bool learned = D.warm_start == TDS_WARM_LEARNED;
+  // the learned warm start also reads the previous step's impulses
+  int use_prev = (D.warm_start != TDS_WARM_COLD) && s->have_prev;
+  launches += tds_launch_narrowphase(d, s->k, use_prev, s->st);
+  launches += tds_launch_predict(d, s->k, s->st);
+  if (E) CUDA_TRY(cudaEventRecord(E[2], s->st));
+  launches += tds_launch_colouring(d, s->L.n, s->L.cap, s->colour_blocks, 256, s->st);
+  d.targ = s->recording ? s->x.targ : nullptr;
+  if (learned || s->recording) launches += tds_launch_features(d, s->k, s->x.surf, s->L.ncols, s->L.cap, s->st);
+  if (learned) {
+    tds_launch_learned(d, s->x.packed, s->L.cap, s->st);
+    launches += 1;
+  }
+  launches += tds_launch_bucketing(d, s->L.cap, s->st);
+  if (E) CUDA_TRY(cudaEventRecord(E[3], s->st));
+  CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned, s->pgs_blocks,
+                          s->st));
+  launches += 1;
+  if (E) CUDA_TRY(cudaEventRecord(E[4], s->st));
+  launches += tds_launch_finish(d, s->k, s->L.cap, s->st);
+  if (E) CUDA_TRY(cudaEventRecord(E[5], s->st));
+  std::swap(d.prev_first[0], d.prev_first[1]);
+  std::swap(d.prev_cnt[0], d.prev_cnt[1]);
+  std::swap(d.prev_other[0], d.prev_other[1]);
+  std::swap(d.prev_l0[0], d.prev_l0[1]);
+  std::swap(d.prev_l1[0], d.prev_l1[1]);
+  return TDS_OK;
+}
+
+GraphKey graph_key(const tds_scene *s) {
+  GraphKey g;
+  g.use_prev = (s->desc.warm_start != TDS_WARM_COLD) && s->have_prev;
+  g.warm = s->desc.warm_start;
+  g.recording = s->recording;
+  g.max_iters = s->desc.max_iters;
+  g.every = s->desc.residual_every;
+  g.tol = s->desc.tol;
+  return g;
+}
+
+// One step replayed from a graph captured on first use (and again whenever
+// the settings it baked in change). Two graphs alternate because the step
+// swaps its double buffers; phase timing collapses to the whole step.
+tds_status step_graph(tds_scene *s, cudaEvent_t *E) {
+  StepGraph &g = s->graphs[s->parity];
+  const GraphKey key = graph_key(s);
+  if (!g.exec || !(g.key == key)) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    DevPtrs saved = s->d;
+    cudaGraph_t graph = nullptr;
+    uint64_t launches = 0;
+    CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
+    tds_status r = enqueue_step(s, nullptr, launches);
+    cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    s->d = saved;  // enqueue_step swapped the buffers; the replay below swaps them
+    if (r != TDS_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (ce != cudaSuccess) return fail(TDS_ERR_CUDA, std::string("capturing the step: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(TDS_ERR_CUDA, std::string("instantiating the step: ") + cudaGetErrorString(ce));
+    g.key = key;
+    g.launches = launches;
+  }
+  if (E) CUDA_TRY(cudaEventRecord(E[0], s->st));
+  CUDA_TRY(cudaGraphLaunch(g.exec, s->st));
+  if (E) {
+    for (int q = 1; q < 5; ++q) CUDA_TRY(cudaEventRecord(E[q], s->st));
+    CUDA_TRY(cudaEventRecord(E[5], s->st));
+  }
+  s->launches += g.launches;
+  DevPtrs &d = s->d;  // the same swaps as the captured step
+  std::swap(d.pos, d.pos2);
+  std::swap(d.pv, d.pv2);
+  std::swap(d.pid, d.pid2);
+  std::swap(d.sid, d.sid2);
+  std::swap(d.prev_first[0], d.prev_first[1]);
+  std::swap(d.prev_cnt[0], d.prev_cnt[1]);
+  std::swap(d.prev_other[0], d.prev_other[1]);
+  std::swap(d.prev_l0[0], d.prev_l0[1]);
+  std::swap(d.prev_l1[0], d.prev_l1[1]);
+  d.targ = s->recording ? s->x.targ : nullptr;
+  return TDS_OK;
+}
+
+tds_status read_particles_impl(tds_scene *s, uint32_t off, uint32_t count, float *x, float *y, float *z,
+                               float *vx, float *vy, float *vz, float *wx, float *wy, float *wz) {
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  tds_launch_stage(s->d, s->L.n, s->st);
+  float *outs[9] = {x, y, z, vx, vy, vz, wx, wy, wz};
+  for (int q = 0; q < 9; ++q)
+    if (outs[q])
+      CUDA_TRY(cudaMemcpyAsync(outs[q], s->d.stage + (size_t)q * s->L.n + off, sizeof(float) * count,
+                               cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+}  // namespace
+
+// Lets other translation units of the library report through tds_last_error.
+tds_status tds_set_error_message(tds_status s, const char *msg) { return fail(s, msg); }
+
+extern "C" {
+
+const char *tds_last_error(void) { return g_err.c_str(); }
+
+tds_status tds_workspace_bytes(const tds_scene_desc *desc, uint64_t *bytes) {
+  return workspace_bytes_impl(desc, desc ? 1u : 0u, bytes);
+}
+
+tds_status tds_batch_workspace_bytes(const tds_scene_desc *descs, uint32_t count, uint64_t *bytes) {
+  return workspace_bytes_impl(descs, count, bytes);
+}
+
+tds_status tds_create_scene(const tds_scene_desc *desc, void *workspace, uint64_t workspace_bytes,
+                            void *stream, tds_scene **out) {
+  if (!desc) return fail(TDS_ERR_INVALID_ARG, "desc is NULL");
+  return create_impl(desc, 1, workspace, workspace_bytes, stream, out);
+}
+
+tds_status tds_create_batch(const tds_scene_desc *descs, uint32_t count, void *workspace,
+                            uint64_t workspace_bytes, void *stream, tds_scene **out) {
+  return create_impl(descs, count, workspace, workspace_bytes, stream, out);
+}
+
+tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[4],
+                             const float linvel[3], const float angvel[3]) {
+  return set_pose_impl(s, 0, pos, quat, linvel, angvel);
+}
+
+tds_status tds_batch_set_tool_pose(tds_scene *s, uint32_t scene, const float pos[3], const float quat[4],
+                                   const float linvel[3], const float angvel[3]) {
+  return set_pose_impl(s, scene, pos, quat, linvel, angvel);
+}
+
+tds_status tds_batch_set_tool_poses(tds_scene *s, const float *poses, uint32_t count) {
+  if (!s || !poses) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (count != s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "count differs from the batch size");
+  for (uint32_t q = 0; q < count; ++q) {
+    const float *p = poses + 13 * (size_t)q;
+    tds_status r = set_pose_impl(s, q, p, p + 3, p + 7, p + 10);
+    if (r != TDS_OK) return r;
+  }
   return TDS_OK;
 }
 
@@ -529,15 +793,28 @@ tds_status tds_set_warm_start(tds_scene *s, int32_t mode) {
   return TDS_OK;
 }
 
+tds_status tds_set_graph(tds_scene *s, int32_t enable) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (enable && (s->st == nullptr || s->st == cudaStreamLegacy || s->st == cudaStreamPerThread))
+    return fail(TDS_ERR_INVALID_ARG, "graph replay needs a created (non-default) stream");
+  s->graph = enable != 0;
+  return TDS_OK;
+}
+
 tds_status tds_step(tds_scene *s, uint32_t nsteps) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
   tds_status ls = check_latched(s);
   if (ls != TDS_OK) return ls;
   if (s->desc.warm_start == TDS_WARM_LEARNED && !s->have_weights)
     return fail(TDS_ERR_STATE, "TDS_WARM_LEARNED needs tds_set_mlp_weights first");
-  const tds_scene_desc &D = s->desc;
   for (uint32_t it = 0; it < nsteps; ++it) {
-    DevPtrs &d = s->d;
+    if (s->geo_dirty) {  // tool poses changed: new world boxes and tool motion
+      CUDA_TRY(cudaMemcpyAsync(s->x.boxes, s->host_boxes.data(), sizeof(BoxF) * s->host_boxes.size(),
+                               cudaMemcpyHostToDevice, s->st));
+      CUDA_TRY(cudaMemcpyAsync(s->x.geo, s->L.geo.data(), sizeof(SceneGeo) * s->L.geo.size(),
+                               cudaMemcpyHostToDevice, s->st));
+      s->geo_dirty = false;
+    }
     cudaEvent_t *E = nullptr;
     if (s->timing) {
       while (s->ev.size() < s->ev_used + 6) {
@@ -547,42 +824,10 @@ tds_status tds_step(tds_scene *s, uint32_t nsteps) {
       }
       E = s->ev.data() + s->ev_used;
       s->ev_used += 6;
-      CUDA_TRY(cudaEventRecord(E[0], s->st));
     }
-    s->launches += tds_launch_broadphase(d, s->k, s->sz.ncells, s->st);
-    std::swap(d.pos, d.pos2);
-    std::swap(d.pv, d.pv2);
-    std::swap(d.pid, d.pid2);
-    if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
-    const bool learned = D.warm_start == TDS_WARM_LEARNED;
-    // the learned warm start also reads the previous step's impulses
-    int use_prev = (D.warm_start != TDS_WARM_COLD) && s->have_prev;
-    s->launches += tds_launch_narrowphase(d, s->k, use_prev, s->st);
-    s->launches += tds_launch_predict(d, s->k, s->st);
-    if (E) CUDA_TRY(cudaEventRecord(E[2], s->st));
-    s->launches += tds_launch_colouring(d, s->sz.n, s->sz.cap, s->colour_blocks, 256, s->st);
-    d.targ = s->recording ? s->x.targ : nullptr;
-    if (learned || s->recording) {
-      tds_launch_features(d, s->k, s->sz.mq, s->x.surf, s->sz.cap, s->st);
-      s->launches += s->sz.mq.cf > 0 ? 3 : 1;
-    }
-    if (learned) {
-      tds_launch_learned(d, s->x.packed, s->sz.cap, s->st);
-      s->launches += 1;
-    }
-    s->launches += tds_launch_bucketing(d, s->sz.cap, s->st);
-    if (E) CUDA_TRY(cudaEventRecord(E[3], s->st));
-    CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned,
-                            s->pgs_blocks, s->st));
-    s->launches += 1;
-    if (E) CUDA_TRY(cudaEventRecord(E[4], s->st));
-    s->launches += tds_launch_finish(d, s->k, s->sz.cap, s->st);
-    if (E) CUDA_TRY(cudaEventRecord(E[5], s->st));
-    std::swap(d.prev_first[0], d.prev_first[1]);
-    std::swap(d.prev_cnt[0], d.prev_cnt[1]);
-    std::swap(d.prev_other[0], d.prev_other[1]);
-    std::swap(d.prev_l0[0], d.prev_l0[1]);
-    std::swap(d.prev_l1[0], d.prev_l1[1]);
+    tds_status r = s->graph ? step_graph(s, E) : enqueue_step(s, E, s->launches);
+    if (r != TDS_OK) return r;
+    s->parity ^= 1u;
     s->have_prev = true;
     s->steps++;
   }
@@ -600,16 +845,16 @@ tds_status tds_synchronize(tds_scene *s) {
 tds_status tds_read_particles(tds_scene *s, float *x, float *y, float *z, float *vx, float *vy,
                               float *vz, float *wx, float *wy, float *wz, uint32_t n) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
-  if (n != s->sz.n) return fail(TDS_ERR_INVALID_ARG, "n differs from the scene's particle count");
-  tds_status ls = check_latched(s);
-  if (ls != TDS_OK) return ls;
-  tds_launch_stage(s->d, n, s->st);
-  float *outs[9] = {x, y, z, vx, vy, vz, wx, wy, wz};
-  for (int q = 0; q < 9; ++q)
-    if (outs[q])
-      CUDA_TRY(cudaMemcpyAsync(outs[q], s->d.stage + (size_t)q * n, sizeof(float) * n,
-                               cudaMemcpyDeviceToHost, s->st));
-  return sync_and_check(s);
+  if (n != s->L.n) return fail(TDS_ERR_INVALID_ARG, "n differs from the scene's particle count");
+  return read_particles_impl(s, 0, n, x, y, z, vx, vy, vz, wx, wy, wz);
+}
+
+tds_status tds_batch_read_particles(tds_scene *s, uint32_t scene, float *x, float *y, float *z, float *vx,
+                                    float *vy, float *vz, float *wx, float *wy, float *wz, uint32_t n) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (scene >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "scene index out of range");
+  if (n != s->scenes[scene].n) return fail(TDS_ERR_INVALID_ARG, "n differs from that scene's particle count");
+  return read_particles_impl(s, s->scenes[scene].off, n, x, y, z, vx, vy, vz, wx, wy, wz);
 }
 
 tds_status tds_read_tool_force(tds_scene *s, float force[3], float torque[3]) {
@@ -624,6 +869,15 @@ tds_status tds_read_tool_force(tds_scene *s, float force[3], float torque[3]) {
   return TDS_OK;
 }
 
+tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_t count) {
+  if (!s || !force_torque) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (count != s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "count differs from the batch size");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  CUDA_TRY(cudaMemcpyAsync(force_torque, s->d.tool_out, sizeof(float) * 6 * count, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
 tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   if (!s || !out) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
   tds_status ls = check_latched(s);
@@ -636,10 +890,8 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   CUDA_TRY(cudaMemcpyAsync(fs, s->d.fscal, sizeof(fs), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemcpyAsync(acc, s->d.acc, sizeof(acc), cudaMemcpyDeviceToHost, s->st));
   CUDA_TRY(cudaMemsetAsync(s->d.acc, 0, sizeof(acc), s->st));
-  CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bstart, sizeof(uint32_t) * bs.size(),
-                           cudaMemcpyDeviceToHost, s->st));
-  CUDA_TRY(cudaMemcpyAsync(be.data(), s->d.bend, sizeof(uint32_t) * be.size(),
-                           cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(bs.data(), s->d.bstart, sizeof(uint32_t) * bs.size(), cudaMemcpyDeviceToHost, s->st));
+  CUDA_TRY(cudaMemcpyAsync(be.data(), s->d.bend, sizeof(uint32_t) * be.size(), cudaMemcpyDeviceToHost, s->st));
   tds_status r = sync_and_check(s);
   if (r != TDS_OK) return r;
   std::memset(out, 0, sizeof(*out));
@@ -790,6 +1042,8 @@ void tds_destroy_scene(tds_scene *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
+  for (StepGraph &g : s->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->owns && s->mem) cudaFree(s->mem);
   delete s;

@@ -16,12 +16,12 @@ namespace {
 
 __device__ __forceinline__ bool is_dyn(uint32_t b) { return (b & TDS_STATIC) == 0u; }
 
-// Incidence counts per particle and each contact's priority (computed once).
+// Incidence counts per particle (the priorities were written with the
+// contacts).
 __global__ void k_inc_count(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
     uint2 ab = d.c_ab[c];
-    d.prio[c] = priority(d.c_key[c]);
     atomicAdd(d.inc_cnt + ab.x, 1u);
     if (is_dyn(ab.y)) atomicAdd(d.inc_cnt + ab.y, 1u);
   }

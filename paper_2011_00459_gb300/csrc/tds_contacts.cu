@@ -42,16 +42,17 @@ struct HfHit {
   int upper;
 };
 
-__device__ __forceinline__ HfHit hf_distance(const StepConsts &k, float px, float py, float pz) {
-  const int nx = k.hf_nx, ny = k.hf_ny, stride = nx + 1;
-  float tx = __fdiv_rn(__fsub_rn(px, k.hf_x0), k.hf_cell);
-  float ty = __fdiv_rn(__fsub_rn(py, k.hf_y0), k.hf_cell);
+__device__ __forceinline__ HfHit hf_distance(const SceneGeo &G, const float *heights, float px, float py,
+                                             float pz) {
+  const int nx = G.hf_nx, ny = G.hf_ny, stride = nx + 1;
+  float tx = __fdiv_rn(__fsub_rn(px, G.hf_x0), G.hf_cell);
+  float ty = __fdiv_rn(__fsub_rn(py, G.hf_y0), G.hf_cell);
   float fx = floorf(tx), fy = floorf(ty);
   int i, j;
   if (!(fx >= 0.0f)) i = 0; else if (fx > (float)(nx - 1)) i = nx - 1; else i = (int)fx;
   if (!(fy >= 0.0f)) j = 0; else if (fy > (float)(ny - 1)) j = ny - 1; else j = (int)fy;
   float u = __fsub_rn(tx, (float)i), v = __fsub_rn(ty, (float)j);
-  const float *h = k.hf_h;
+  const float *h = heights + G.hf_off;
   HfHit r;
   float hb, uu, vv;
   r.upper = !(__fadd_rn(u, v) <= 1.0f);
@@ -69,8 +70,8 @@ __device__ __forceinline__ HfHit hf_distance(const StepConsts &k, float px, floa
   float e = __fsub_rn(pz, hb);
   e = __fsub_rn(e, __fmul_rn(r.a, uu));
   e = __fsub_rn(e, __fmul_rn(r.b, vv));
-  float num = __fmul_rn(k.hf_cell, e);
-  r.den = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(k.hf_cell, k.hf_cell), __fmul_rn(r.a, r.a)),
+  float num = __fmul_rn(G.hf_cell, e);
+  r.den = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(G.hf_cell, G.hf_cell), __fmul_rn(r.a, r.a)),
                                __fmul_rn(r.b, r.b)));
   r.s = __fdiv_rn(num, r.den);
   return r;
@@ -103,11 +104,16 @@ __device__ __forceinline__ int cell_axis(float x, float x0, float inv, int n) {
   return (int)t;
 }
 
-__device__ __forceinline__ uint32_t cell_index(const StepConsts &k, float4 p, int &cx, int &cy, int &cz) {
-  cx = cell_axis(p.x, k.gx0, k.cell_inv, k.gnx);
-  cy = cell_axis(p.y, k.gy0, k.cell_inv, k.gny);
-  cz = cell_axis(p.z, k.gz0, k.cell_inv, k.gnz);
-  return ((uint32_t)cz * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnx + (uint32_t)cx;
+// Cell of a particle: its scene's block of gnx x gny x gnz cells, then the
+// cell inside it (coordinates clamped to the block, which keeps neighbouring
+// particles in neighbouring cells).
+__device__ __forceinline__ uint32_t cell_index(const StepConsts &k, const SceneGeo &G, uint32_t sid, float4 p,
+                                               int &cx, int &cy, int &cz) {
+  cx = cell_axis(p.x, G.lo[0], k.cell_inv, k.gnx);
+  cy = cell_axis(p.y, G.lo[1], k.cell_inv, k.gny);
+  cz = cell_axis(p.z, G.lo[2], k.cell_inv, k.gnz);
+  const uint32_t cps = (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
+  return sid * cps + ((uint32_t)cz * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnx + (uint32_t)cx;
 }
 
 // ---------------------------------------------------------------------------
@@ -116,7 +122,8 @@ __device__ __forceinline__ uint32_t cell_index(const StepConsts &k, float4 p, in
 __global__ void k_cells(DevPtrs d, StepConsts k) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     int cx, cy, cz;
-    uint32_t c = cell_index(k, d.pos[i], cx, cy, cz);
+    const uint32_t sid = d.sid[i];
+    uint32_t c = cell_index(k, k.geo[sid], sid, d.pos[i], cx, cy, cz);
     d.cell_of[i] = c;
     atomicAdd(d.cell_count + c, 1u);
   }
@@ -150,6 +157,7 @@ __global__ void k_reorder(DevPtrs d, uint32_t n) {
     d.pos2[j] = d.pos[i];
     reinterpret_cast<double4 *>(d.pv2)[j] = reinterpret_cast<const double4 *>(d.pv)[i];
     d.pid2[j] = d.pid[i];
+    d.sid2[j] = d.sid[i];
   }
 }
 
@@ -161,13 +169,15 @@ __global__ void k_reorder(DevPtrs d, uint32_t n) {
 template <class F>
 __device__ __forceinline__ void for_each_contact(const DevPtrs &d, const StepConsts &k, uint32_t i, F &f) {
   const float4 P = d.pos[i];
-  const uint32_t me = d.pid[i];
+  const uint32_t me = d.pid[i], sid = d.sid[i];
+  const SceneGeo &G = k.geo[sid];
   int cx, cy, cz;
-  (void)cell_index(k, P, cx, cy, cz);
+  (void)cell_index(k, G, sid, P, cx, cy, cz);
+  const uint32_t block = sid * (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
   const int x0 = max(cx - 1, 0), x1 = min(cx + 1, k.gnx - 1);
   for (int z = max(cz - 1, 0); z <= min(cz + 1, k.gnz - 1); ++z) {
     for (int y = max(cy - 1, 0); y <= min(cy + 1, k.gny - 1); ++y) {
-      uint32_t row = ((uint32_t)z * (uint32_t)k.gny + (uint32_t)y) * (uint32_t)k.gnx;
+      uint32_t row = block + ((uint32_t)z * (uint32_t)k.gny + (uint32_t)y) * (uint32_t)k.gnx;
       uint32_t s = __ldg(d.cell_start + row + x0), e = __ldg(d.cell_start + row + x1 + 1);
       for (uint32_t j = s; j < e; ++j) {
         uint32_t pj = __ldg(d.pid + j);
@@ -177,23 +187,23 @@ __device__ __forceinline__ void for_each_contact(const DevPtrs &d, const StepCon
       }
     }
   }
-  if (k.hf_nx > 0) {
-    HfHit hit = hf_distance(k, P.x, P.y, P.z);
-    if (hit.s < static_reach(P.w, k.cohesive)) f.hf(hit);
+  if (G.hf_nx > 0) {
+    HfHit hit = hf_distance(G, k.heights, P.x, P.y, P.z);
+    if (hit.s < static_reach(P.w, k.cohesive)) f.hf(G, hit);
   }
-  for (int b = 0; b < k.nb; ++b) {
-    const BoxF &B = k.box[b];
+  for (uint32_t b = 0; b < G.nbox; ++b) {
+    const BoxF &B = k.boxes[G.box0 + b];
     float reach = static_reach(P.w, k.cohesive && !B.is_tool);
     BoxHit hit = box_distance(B, P.x, P.y, P.z);
-    if (hit.d2 < __fmul_rn(reach, reach)) f.box(b, hit);
+    if (hit.d2 < __fmul_rn(reach, reach)) f.box(G, B, b, hit);
   }
 }
 
 struct Counter {
   uint32_t n = 0;
   __device__ void pair(uint32_t, uint32_t, float4) { ++n; }
-  __device__ void hf(const HfHit &) { ++n; }
-  __device__ void box(int, const BoxHit &) { ++n; }
+  __device__ void hf(const SceneGeo &, const HfHit &) { ++n; }
+  __device__ void box(const SceneGeo &, const BoxF &, uint32_t, const BoxHit &) { ++n; }
 };
 
 __global__ void k_count(DevPtrs d, StepConsts k) {
@@ -222,8 +232,8 @@ struct Writer {
   // Common part of every contact: rows and warm start. n points from a
   // towards b (into a static surface), delta is the overlap, vb/wb the other
   // side's velocity at the start of the step.
-  __device__ void emit(uint32_t b_slot, uint32_t other, float3 n, float delta, float rb,
-                       float dstar, float estar, float rbar, float dfloor, bool is_static,
+  __device__ void emit(const SceneGeo &G, uint32_t b_slot, uint32_t other, float3 n, float delta,
+                       float rb, float dstar, float estar, float rbar, float dfloor, bool is_static,
                        bool is_tool, float3 vb, float3 vs, float3 ws) {
     uint32_t c = next++;
     if (c >= k.cap) return;
@@ -238,11 +248,15 @@ struct Writer {
     float Jv0 = dot(n, vb - f3(Va));
     float qn = -4.0f / h * k.ups * g + k.ups * Jv0;
     float fc = (k.cohesive && !is_tool) ? h * k.cohesion * 3.14159265358979f * rbar * rbar : 0.0f;
-    float mu = is_tool ? k.mu_tool : k.mu_t;
-    float rmu = rbar * k.mu_r;
+    float mu = is_tool ? G.mu_tool : G.mu_t;
+    float rmu = rbar * G.mu_r;
     unsigned long long key = ((unsigned long long)me << 32) | other;
     d.c_ab[c] = make_uint2(i, b_slot);
     d.c_key[c] = key;
+    // colouring priority of the scene-local key: a scene of a batch is
+    // coloured exactly as it is alone
+    const uint32_t lo = is_static ? other : other - G.pid0;
+    d.prio[c] = priority(((unsigned long long)(me - G.pid0) << 32) | lo);
     d.c_rn[c] = make_float4(n.x, n.y, n.z, la);
     d.c_rq[c] = make_float4(lb, qn, Sn, fc);
     d.c_rm[c] = make_float2(mu, rmu);
@@ -289,33 +303,33 @@ struct Writer {
     float dstar = 2.0f * P.w * Q.w / rs;
     float4 Vb = d.pv[2 * j];
     float3 z3 = make_float3(0.f, 0.f, 0.f);
-    emit(j, pj, n, delta, Q.w, dstar, k.estar_pair, dstar, 1e-5f * rs, false, false, f3(Vb), z3, z3);
+    emit(k.geo[d.sid[i]], j, pj, n, delta, Q.w, dstar, k.estar_pair, dstar, 1e-5f * rs, false, false,
+         f3(Vb), z3, z3);
   }
 
-  __device__ void surface(uint32_t surf, float3 ns, float s, bool is_tool) {
+  __device__ void surface(const SceneGeo &G, uint32_t surf, float3 ns, float s, bool is_tool) {
     float3 n = make_float3(-ns.x, -ns.y, -ns.z);
     float delta = P.w - s;
     float3 vs = make_float3(0.f, 0.f, 0.f), ws = vs;
     if (is_tool) {
       float la = P.w - 0.5f * delta;
       float3 xc = f3(P) + la * n;
-      float3 rel = xc - make_float3(k.tp[0], k.tp[1], k.tp[2]);
-      ws = make_float3(k.tw[0], k.tw[1], k.tw[2]);
-      vs = make_float3(k.tv[0], k.tv[1], k.tv[2]) + cross(ws, rel);
+      float3 rel = xc - make_float3(G.tp[0], G.tp[1], G.tp[2]);
+      ws = make_float3(G.tw[0], G.tw[1], G.tw[2]);
+      vs = make_float3(G.tv[0], G.tv[1], G.tv[2]) + cross(ws, rel);
     }
-    emit(TDS_STATIC | surf, TDS_STATIC | surf, n, delta, 0.f, 2.0f * P.w, k.estar_static, P.w,
+    emit(G, TDS_STATIC | surf, TDS_STATIC | surf, n, delta, 0.f, 2.0f * P.w, k.estar_static, P.w,
          2e-5f * P.w, true, is_tool, vs, vs, ws);
   }
 
-  __device__ void hf(const HfHit &hit) {
+  __device__ void hf(const SceneGeo &G, const HfHit &hit) {
     float inv = 1.0f / hit.den;
-    float3 ns = hit.upper ? make_float3(hit.a * inv, hit.b * inv, k.hf_cell * inv)
-                          : make_float3(-hit.a * inv, -hit.b * inv, k.hf_cell * inv);
-    surface(0u, ns, hit.s, false);
+    float3 ns = hit.upper ? make_float3(hit.a * inv, hit.b * inv, G.hf_cell * inv)
+                          : make_float3(-hit.a * inv, -hit.b * inv, G.hf_cell * inv);
+    surface(G, 0u, ns, hit.s, false);
   }
 
-  __device__ void box(int b, const BoxHit &hit) {
-    const BoxF &B = k.box[b];
+  __device__ void box(const SceneGeo &G, const BoxF &B, uint32_t b, const BoxHit &hit) {
     float3 ns;
     float s;
     if (hit.d2 > 0.0f) {
@@ -335,7 +349,7 @@ struct Writer {
       s = -depth;
       ns = make_float3(side * B.R[ax], side * B.R[3 + ax], side * B.R[6 + ax]);
     }
-    surface((uint32_t)(1 + b), ns, s, B.is_tool != 0);
+    surface(G, 1u + b, ns, s, B.is_tool != 0);
   }
 };
 

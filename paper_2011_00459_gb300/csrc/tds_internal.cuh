@@ -27,29 +27,40 @@ struct BoxF {
   int is_tool;
 };
 
+// Geometry and material of one scene of a batch (device table; a single
+// scene is a batch of one). Scenes never touch: each has its own block of
+// broadphase cells, so its particles keep their own coordinates.
+struct SceneGeo {
+  float lo[3];                 // origin of the scene's broadphase cells
+  int hf_nx, hf_ny;            // heightfield (hf_nx == 0: none)
+  float hf_x0, hf_y0, hf_cell;
+  uint32_t hf_off;             // first height of the scene in the heights array
+  uint32_t box0, nbox, nwall;  // its boxes in the box table, walls first
+  float mu_t, mu_tool, mu_r;
+  float tp[3], tv[3], tw[3];   // tool motion (point velocity v_T + w_T x (x - p_T))
+  int cf, ncx, ncy;            // surface columns of the learned warm start (cf 0: none)
+  uint32_t col_off;            // first column of the scene in the surface array
+  uint32_t pid0;               // first particle id of the scene (ids are global)
+};
+
 // Per-step constants, passed by value to every kernel.
 struct StepConsts {
-  uint32_t n;           // particles
+  uint32_t n;           // particles (all scenes)
   uint32_t cap;         // contact capacity
+  uint32_t nscenes;
   float dt, g[3];
   float ups;            // Upsilon = 1 / (1 + 4 tau / dt), tau = 2 dt
   float estar_pair;     // [2 (1 - nu^2) / E]^-1
   float estar_static;   // E / (1 - nu^2)
-  float mu_t, mu_tool, mu_r, cohesion;
+  float cohesion;
   int cohesive;
   float sig_t, sig_r;   // gamma_t / dt, gamma_r / dt
-  // broadphase grid
-  float gx0, gy0, gz0, cell_inv;
+  // broadphase: every scene has gnx x gny x gnz cells of width 1/cell_inv
+  float cell_inv;
   int gnx, gny, gnz;
-  // heightfield
-  int hf_nx, hf_ny;
-  float hf_x0, hf_y0, hf_cell;
-  const float *hf_h;
-  // boxes
-  int nb, n_walls;
-  BoxF box[TDS_MAX_BOXES];
-  // tool motion (point velocity v_T + w_T x (x - p_T))
-  float tp[3], tv[3], tw[3];
+  const SceneGeo *geo;
+  const BoxF *boxes;    // world-frame boxes of all scenes
+  const float *heights; // heightfields of all scenes
 };
 
 // Device pointers of one scene (passed by value).
@@ -58,8 +69,9 @@ struct DevPtrs {
   float4 *pos;                // (x, y, z, r)
   float4 *pv;                 // 32-byte state record per particle: [2i] (v, 1/m), [2i+1] (w, 1/I)
   uint32_t *pid;
+  uint32_t *sid;              // scene of the particle
   float4 *pos2, *pv2;         // reorder targets
-  uint32_t *pid2;
+  uint32_t *pid2, *sid2;
   // grid
   uint32_t *cell_of, *cell_count, *cell_start, *cell_cursor, *perm;
   // contacts in owner order (owner = the particle with the smaller id)
@@ -101,7 +113,8 @@ struct DevPtrs {
   uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
   uint32_t *scan_tmp;
   float *stage;               // 9 n floats for reads
-  float *tool_out;            // 6 floats
+  float *tool_out;            // 6 floats per scene
+  double *tool_acc;           // per-scene force and torque accumulators (batches)
   // learned warm start (owner order)
   float *feat;                // 10 features per contact
   float4 *sdirw;              // slip direction s and impulse scale W per contact
@@ -109,11 +122,7 @@ struct DevPtrs {
   uint8_t *c_flag;            // 1 if the contact's key existed in the previous step
 };
 
-// Surface columns of the learned warm start's depth feature: heightfield
-// cells grouped cf x cf (cf = 0: no heightfield, depth 0).
-struct MlpConsts {
-  int cf, ncx, ncy;
-};
+
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_COUNT = 16 };

@@ -354,26 +354,28 @@ __device__ __forceinline__ int ordered(float f) {  // float -> int with the same
 }
 __device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
 
-// Column of a centre: heightfield cells grouped f x f, FP32 with explicit
-// rounding (the same decision as the oracle's).
-__device__ __forceinline__ int column_of(const StepConsts &k, const MlpConsts &q, float px, float py) {
-  const float w = __fmul_rn(k.hf_cell, (float)q.cf);
-  const float tx = __fdiv_rn(__fsub_rn(px, k.hf_x0), w), ty = __fdiv_rn(__fsub_rn(py, k.hf_y0), w);
+// Column of a centre in its scene: heightfield cells grouped cf x cf, FP32
+// with explicit rounding (the same decision as the oracle's).
+__device__ __forceinline__ uint32_t column_of(const SceneGeo &G, float px, float py) {
+  const float w = __fmul_rn(G.hf_cell, (float)G.cf);
+  const float tx = __fdiv_rn(__fsub_rn(px, G.hf_x0), w), ty = __fdiv_rn(__fsub_rn(py, G.hf_y0), w);
   const float fx = floorf(tx), fy = floorf(ty);
   int i, j;
-  if (!(fx >= 0.0f)) i = 0; else if (fx > (float)(q.ncx - 1)) i = q.ncx - 1; else i = (int)fx;
-  if (!(fy >= 0.0f)) j = 0; else if (fy > (float)(q.ncy - 1)) j = q.ncy - 1; else j = (int)fy;
-  return j * q.ncx + i;
+  if (!(fx >= 0.0f)) i = 0; else if (fx > (float)(G.ncx - 1)) i = G.ncx - 1; else i = (int)fx;
+  if (!(fy >= 0.0f)) j = 0; else if (fy > (float)(G.ncy - 1)) j = G.ncy - 1; else j = (int)fy;
+  return G.col_off + (uint32_t)(j * G.ncx + i);
 }
 
-__global__ void k_columns_clear(MlpConsts q, int *surf) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.ncx * q.ncy; c += gridDim.x * blockDim.x)
+__global__ void k_columns_clear(uint32_t ncols, int *surf) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncols; c += gridDim.x * blockDim.x)
     surf[c] = ordered(-INFINITY);
 }
-__global__ void k_columns(DevPtrs d, StepConsts k, MlpConsts q, int *surf) {
+__global__ void k_columns(DevPtrs d, StepConsts k, int *surf) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
+    const SceneGeo &G = k.geo[d.sid[i]];
+    if (G.cf <= 0) continue;
     const float4 P = d.pos[i];
-    atomicMax(surf + column_of(k, q, P.x, P.y), ordered(__fadd_rn(P.z, P.w)));
+    atomicMax(surf + column_of(G, P.x, P.y), ordered(__fadd_rn(P.z, P.w)));
   }
 }
 
@@ -389,7 +391,7 @@ __device__ __forceinline__ float3 axis_tangent(float3 n) {
 
 // Features of every contact (owner order) at v* with the previous-step
 // impulses; also the slip direction s and the scale W for the outputs.
-__global__ void k_features(DevPtrs d, StepConsts k, MlpConsts q, const int *surf) {
+__global__ void k_features(DevPtrs d, StepConsts k, const int *surf) {
   const uint32_t nc = d.ctr[CTR_NC];
   const float gh = sqrtf(k.g[0] * k.g[0] + k.g[1] * k.g[1] + k.g[2] * k.g[2]) * k.dt;
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
@@ -399,6 +401,7 @@ __global__ void k_features(DevPtrs d, StepConsts k, MlpConsts q, const int *surf
     const float3 n = f3(rn);
     const float la = rn.w, lb = rq.x;
     const float4 P = d.pos[ab.x];
+    const SceneGeo &G = k.geo[d.sid[ab.x]];
     const float4 va = d.pv[2 * ab.x], wa = d.pv[2 * ab.x + 1];
     float3 vb, wb;
     float imb = 0.f, rb = 0.f;
@@ -421,7 +424,7 @@ __global__ void k_features(DevPtrs d, StepConsts k, MlpConsts q, const int *surf
     onb(n, t1, t2);
     const float3 lt = l0.y * t1 + l0.z * t2;
     float depth = 0.f;
-    if (q.cf > 0) depth = (unordered(surf[column_of(k, q, P.x, P.y)]) - P.z) / dbar;
+    if (G.cf > 0) depth = (unordered(surf[column_of(G, P.x, P.y)]) - P.z) / dbar;
     const uint32_t sid = ab.y & ~TDS_STATIC;
     float *F = d.feat + (size_t)c * 10;
     F[0] = dot(n, dv) / gh;
@@ -433,7 +436,7 @@ __global__ void k_features(DevPtrs d, StepConsts k, MlpConsts q, const int *surf
     F[6] = (float)d.inc_cnt[ab.x];
     F[7] = dyn ? (float)d.inc_cnt[ab.y] : 0.f;
     F[8] = depth;
-    F[9] = dyn ? 0.f : (sid >= 1u + (uint32_t)k.n_walls ? 2.f : 1.f);
+    F[9] = dyn ? 0.f : (sid >= 1u + G.nwall ? 2.f : 1.f);
     d.sdirw[c] = make_float4(s.x, s.y, s.z, W);
   }
 }
@@ -480,15 +483,18 @@ __global__ void __launch_bounds__(256) k_learned(DevPtrs d, const Packed *gP) {
 
 }  // namespace
 
-void tds_launch_features(const DevPtrs &d, const StepConsts &k, const MlpConsts &q, int *surf,
-                         uint32_t cap, cudaStream_t st) {
-  if (q.cf > 0) {
-    k_columns_clear<<<(q.ncx * q.ncy + 255) / 256, 256, 0, st>>>(q, surf);
-    k_columns<<<(k.n + 255) / 256, 256, 0, st>>>(d, k, q, surf);
+int tds_launch_features(const DevPtrs &d, const StepConsts &k, int *surf, uint32_t ncols, uint32_t cap,
+                        cudaStream_t st) {
+  int launches = 1;
+  if (ncols > 0) {
+    k_columns_clear<<<(ncols + 255) / 256, 256, 0, st>>>(ncols, surf);
+    k_columns<<<(k.n + 255) / 256, 256, 0, st>>>(d, k, surf);
+    launches += 2;
   }
   unsigned blocks = (cap + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_features<<<blocks, 256, 0, st>>>(d, k, q, surf);
+  k_features<<<blocks, 256, 0, st>>>(d, k, surf);
+  return launches;
 }
 void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, cudaStream_t st) {
   unsigned blocks = (cap + 127) / 128;

@@ -530,19 +530,27 @@ __global__ void k_tool_partial(DevPtrs d, StepConsts k) {
   __shared__ double sh[8];
   const uint32_t np = d.ctr[CTR_PADDED];
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  const uint32_t first_tool = 1u + (uint32_t)k.n_walls;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     if (d.order[p] == 0xFFFFFFFFu) continue;  // padding slot
     uint2 ab = d.p_ab[p];
-    if (is_dyn(ab.y) || (ab.y & ~TDS_STATIC) < first_tool) continue;
+    if (is_dyn(ab.y)) continue;
+    const uint32_t sid = d.sid[ab.x];
+    const SceneGeo &G = k.geo[sid];
+    if ((ab.y & ~TDS_STATIC) < 1u + G.nwall) continue;
     float4 rn = d.p_rn[p], L0 = d.p_la[p];
     float2 L1 = d.p_lb[p];
     float3 n = f3(rn), t1, t2;
     onb(n, t1, t2);
     float3 F = (1.0f / k.dt) * (L0.x * n + L0.y * t1 + L0.z * t2);
     float3 xc = f3(d.pos[ab.x]) + rn.w * n;
-    float3 arm = xc - make_float3(k.tp[0], k.tp[1], k.tp[2]);
+    float3 arm = xc - make_float3(G.tp[0], G.tp[1], G.tp[2]);
     float3 T = cross(arm, F) + (1.0f / k.dt) * make_float3(L0.w, L1.x, L1.y);
+    if (k.nscenes > 1) {  // batches: per-scene accumulators
+      double *dst = d.tool_acc + 6 * (size_t)sid;
+      atomicAdd(dst + 0, (double)F.x); atomicAdd(dst + 1, (double)F.y); atomicAdd(dst + 2, (double)F.z);
+      atomicAdd(dst + 3, (double)T.x); atomicAdd(dst + 4, (double)T.y); atomicAdd(dst + 5, (double)T.z);
+      continue;
+    }
     acc[0] += F.x; acc[1] += F.y; acc[2] += F.z;
     acc[3] += T.x; acc[4] += T.y; acc[5] += T.z;
   }
@@ -552,11 +560,18 @@ __global__ void k_tool_partial(DevPtrs d, StepConsts k) {
   }
 }
 
-__global__ void k_tool_final(DevPtrs d) {
-  if (threadIdx.x < 6) {
-    double t = 0.0;
-    for (int b = 0; b < kToolBlocks; ++b) t += d.dpart[6 * b + threadIdx.x];
-    d.tool_out[threadIdx.x] = (float)t;
+__global__ void k_tool_final(DevPtrs d, uint32_t nscenes) {
+  if (nscenes == 1) {
+    if (threadIdx.x < 6) {
+      double t = 0.0;
+      for (int b = 0; b < kToolBlocks; ++b) t += d.dpart[6 * b + threadIdx.x];
+      d.tool_out[threadIdx.x] = (float)t;
+    }
+    return;
+  }
+  for (uint32_t q = threadIdx.x; q < 6 * nscenes; q += blockDim.x) {
+    d.tool_out[q] = (float)d.tool_acc[q];
+    d.tool_acc[q] = 0.0;
   }
 }
 
@@ -614,7 +629,7 @@ int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaS
   k_writeback<<<grid_for(cap, 256), 256, 0, st>>>(d);
   k_prev_ranges<<<grid_for(k.n, 256), 256, 0, st>>>(d, k.n, cap);
   k_tool_partial<<<kToolBlocks, 256, 0, st>>>(d, k);
-  k_tool_final<<<1, 32, 0, st>>>(d);
+  k_tool_final<<<1, 256, 0, st>>>(d, k.nscenes);
   k_integrate<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
   return 5;
 }

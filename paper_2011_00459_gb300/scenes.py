@@ -367,6 +367,41 @@ def large(seed: int = 0, n: int = 1000000) -> dict:
     return s
 
 
+def batched_bed(n: int, r_lo: float, r_hi: float, depth0: float, speed: float,
+                blade_depth: float, mu_t: float, seed: int) -> dict:
+    """One bed of a batch: n spheres on a 2:1 walled footprint sized so the
+    spawn lattice is about depth0 deep, on a flat heightfield (0.05 m cells),
+    mu_r 0.1, no cohesion, blade 0.8 ly x 0.3 x 0.02 m."""
+    s_lat = 2.1 * r_hi
+    area = n / (depth0 / s_lat) * s_lat * s_lat
+    ly = max(math.sqrt(0.5 * area), 4.0 * s_lat)
+    lx = 2.0 * ly
+    nx = int(math.ceil((lx + 0.6) / 0.05))
+    ny = int(math.ceil((ly + 0.6) / 0.05))
+    p = base_params(mu_t=mu_t, mu_r=0.1, cohesion=0.0, iters=50,
+                    hf=flat_heightfield(nx, ny, -0.3, -0.3, 0.05),
+                    walls=bed_walls(lx, ly, 3.0 * depth0 + 2.0),
+                    tool_boxes=blade(0.8 * ly, 0.3, 0.02))
+    s = _spawned(p, n, lx, ly, r_lo, r_hi, seed, 0.0)
+    s.update(name="batched-bed", footprint=(lx, ly), blade_speed=speed, blade_depth=blade_depth,
+             blade_height=0.3, tool_kind="blade", settle_steps=300)
+    return s
+
+
+def batched(seed: int = 0, scenes: int = 256, n_lo: int = 1000, n_hi: int = 20000) -> list:
+    """Independent beds for one batch: n ~ log-U[n_lo, n_hi] (mean ~6.3e3 for
+    the defaults, ~1.6e6 spheres in 256 beds), r ~ U[0.03, 0.05] m, 2:1
+    footprints 0.6 m deep before settling, blade speed U[0.2, 1.5] m/s,
+    depth U[0.1, 0.4] m, mu_t U[0.4, 0.9]; dt = 1/60 s, 50 sweeps."""
+    g = rng(seed)
+    ns = np.exp(g.uniform(math.log(n_lo), math.log(n_hi), scenes)).astype(np.int64)
+    speed = g.uniform(0.2, 1.5, scenes)
+    depth = g.uniform(0.1, 0.4, scenes)
+    mu = g.uniform(0.4, 0.9, scenes)
+    return [batched_bed(int(ns[q]), 0.03, 0.05, 0.6, float(speed[q]), float(depth[q]), float(mu[q]),
+                        1000 * seed + q + 1) for q in range(scenes)]
+
+
 WORKLOADS = {"small": small, "bulldozing": bulldozing, "excavation": excavation,
              "large": large}
 

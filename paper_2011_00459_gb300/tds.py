@@ -29,7 +29,9 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_last_error", "tds_find_pair_contacts_noalloc", "tds_mlp_param_count",
             "tds_set_mlp_weights", "tds_set_recording", "tds_read_training_samples",
             "tds_mlp_workspace_bytes", "tds_mlp_forward", "tds_mlp_loss_grad", "tds_mlp_adam_step",
-            "tds_set_warm_start"]
+            "tds_set_warm_start", "tds_batch_workspace_bytes", "tds_create_batch",
+            "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
+            "tds_set_graph", "tds_batch_set_tool_poses"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -113,6 +115,15 @@ def lib() -> ctypes.CDLL:
         L.tds_mlp_forward.argtypes = [vp, vp, ctypes.c_uint32, vp, vp, vp]
         L.tds_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, vp, vp]
         L.tds_mlp_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_uint32, ctypes.c_float, vp]
+        L.tds_batch_workspace_bytes.argtypes = [ctypes.POINTER(SceneDesc), ctypes.c_uint32,
+                                                ctypes.POINTER(ctypes.c_uint64)]
+        L.tds_create_batch.argtypes = [ctypes.POINTER(SceneDesc), ctypes.c_uint32, vp, ctypes.c_uint64, vp,
+                                       ctypes.POINTER(vp)]
+        L.tds_batch_set_tool_pose.argtypes = [vp, ctypes.c_uint32, _fp, _fp, _fp, _fp]
+        L.tds_batch_read_particles.argtypes = [vp, ctypes.c_uint32] + [vp] * 9 + [ctypes.c_uint32]
+        L.tds_batch_read_tool_forces.argtypes = [vp, vp, ctypes.c_uint32]
+        L.tds_set_graph.argtypes = [vp, ctypes.c_int32]
+        L.tds_batch_set_tool_poses.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_destroy_scene.argtypes = [vp]
         L.tds_destroy_scene.restype = None
         L.tds_last_error.restype = ctypes.c_char_p
@@ -141,6 +152,56 @@ def _vec(a, n):
     return (_f * n)(*[float(v) for v in a])
 
 
+def _make_desc(s: dict, contacts_per_particle: int, domain):
+    """tds_scene_desc of a scene dictionary; returns (desc, arrays to keep alive, n)."""
+    x = _f32(s["x"]).reshape(-1, 3)
+    n = x.shape[0]
+    keep = []
+
+    def col(a, k):
+        c = np.ascontiguousarray(a[:, k])
+        keep.append(c)
+        return _fptr(c)
+
+    v = _f32(s.get("v", np.zeros((n, 3)))).reshape(n, 3)
+    w = _f32(s.get("w", np.zeros((n, 3)))).reshape(n, 3)
+    r = _f32(s["r"]).reshape(n)
+    keep.append(r)
+    d = SceneDesc()
+    d.n = n
+    d.x, d.y, d.z = col(x, 0), col(x, 1), col(x, 2)
+    d.vx, d.vy, d.vz = col(v, 0), col(v, 1), col(v, 2)
+    d.wx, d.wy, d.wz = col(w, 0), col(w, 1), col(w, 2)
+    d.radius = _fptr(r)
+    d.density, d.young, d.poisson = s["density"], s["young"], s["poisson"]
+    d.mu_t, d.mu_r, d.cohesion = s["mu_t"], s["mu_r"], s["cohesion"]
+    d.mu_tool = s.get("mu_tool", s["mu_t"])
+    hf = s.get("hf")
+    if hf is not None:
+        h = _f32(hf["h"]).reshape(-1)
+        keep.append(h)
+        d.hf_nx, d.hf_ny = hf["nx"], hf["ny"]
+        d.hf_x0, d.hf_y0, d.hf_cell = hf["x0"], hf["y0"], hf["cell"]
+        d.hf_heights = _fptr(h)
+    walls = _f32(s.get("walls", np.zeros((0, 10)))).reshape(-1, 10)
+    boxes = _f32(s.get("tool_boxes", np.zeros((0, 10)))).reshape(-1, 10)
+    keep += [walls, boxes]
+    d.n_walls, d.walls = walls.shape[0], _fptr(walls)
+    d.n_tool_boxes, d.tool_boxes = boxes.shape[0], _fptr(boxes)
+    d.dt = s["dt"]
+    for i in range(3):
+        d.gravity[i] = s["gravity"][i]
+    d.max_iters = int(s["iters"])
+    d.tol = float(s.get("tol", 0.0))
+    d.residual_every = int(s.get("residual_every", 10))
+    d.warm_start = int(s.get("warm_start", 1))
+    d.contacts_per_particle = int(contacts_per_particle)
+    if domain is not None:
+        for i in range(3):
+            d.domain_lo[i], d.domain_hi[i] = domain[0][i], domain[1][i]
+    return d, keep, n
+
+
 class Scene:
     """One simulated bed on the current CUDA device.
 
@@ -151,59 +212,30 @@ class Scene:
 
     def __init__(self, scene: dict, stream=None, workspace: str = "torch",
                  contacts_per_particle: int = 0, domain=None, **override):
+        s = dict(scene)
+        s.update(override)
+        self._create([s], stream, workspace, contacts_per_particle, [domain])
+        if "tool" in s and s["tool"] is not None:
+            self.set_tool_pose(s["tool"])
+
+    def _create(self, scenes, stream, workspace, contacts_per_particle, domains):
         import torch
 
         if not torch.cuda.is_available():
             raise TdsError(-2, "no CUDA device")
-        s = dict(scene)
-        s.update(override)
-        x = _f32(s["x"]).reshape(-1, 3)
-        n = x.shape[0]
-        keep = []
-
-        def col(a, k):
-            c = np.ascontiguousarray(a[:, k])
-            keep.append(c)
-            return _fptr(c)
-
-        v = _f32(s.get("v", np.zeros((n, 3)))).reshape(n, 3)
-        w = _f32(s.get("w", np.zeros((n, 3)))).reshape(n, 3)
-        r = _f32(s["r"]).reshape(n)
-        keep.append(r)
-        d = SceneDesc()
-        d.n = n
-        d.x, d.y, d.z = col(x, 0), col(x, 1), col(x, 2)
-        d.vx, d.vy, d.vz = col(v, 0), col(v, 1), col(v, 2)
-        d.wx, d.wy, d.wz = col(w, 0), col(w, 1), col(w, 2)
-        d.radius = _fptr(r)
-        d.density, d.young, d.poisson = s["density"], s["young"], s["poisson"]
-        d.mu_t, d.mu_r, d.cohesion = s["mu_t"], s["mu_r"], s["cohesion"]
-        d.mu_tool = s.get("mu_tool", s["mu_t"])
-        hf = s.get("hf")
-        if hf is not None:
-            h = _f32(hf["h"]).reshape(-1)
-            keep.append(h)
-            d.hf_nx, d.hf_ny = hf["nx"], hf["ny"]
-            d.hf_x0, d.hf_y0, d.hf_cell = hf["x0"], hf["y0"], hf["cell"]
-            d.hf_heights = _fptr(h)
-        walls = _f32(s.get("walls", np.zeros((0, 10)))).reshape(-1, 10)
-        boxes = _f32(s.get("tool_boxes", np.zeros((0, 10)))).reshape(-1, 10)
-        keep += [walls, boxes]
-        d.n_walls, d.walls = walls.shape[0], _fptr(walls)
-        d.n_tool_boxes, d.tool_boxes = boxes.shape[0], _fptr(boxes)
-        d.dt = s["dt"]
-        for i in range(3):
-            d.gravity[i] = s["gravity"][i]
-        d.max_iters = int(s["iters"])
-        d.tol = float(s.get("tol", 0.0))
-        d.residual_every = int(s.get("residual_every", 10))
-        d.warm_start = int(s.get("warm_start", 1))
-        d.contacts_per_particle = int(contacts_per_particle)
-        if domain is not None:
-            for i in range(3):
-                d.domain_lo[i], d.domain_hi[i] = domain[0][i], domain[1][i]
-        self.n = n
-        self.desc = d
+        count = len(scenes)
+        descs = (SceneDesc * count)()
+        keep, sizes = [], []
+        for q, s in enumerate(scenes):
+            d, k, n = _make_desc(s, contacts_per_particle, domains[q])
+            descs[q] = d
+            keep += k
+            sizes.append(n)
+        self.sizes = sizes
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        self.desc = descs[0]
+        self._descs = descs
         self._keep = keep
         L = lib()
         self._torch = torch
@@ -212,17 +244,19 @@ class Scene:
         ws_ptr, ws_bytes = None, 0
         if workspace == "torch":
             nb = ctypes.c_uint64()
-            _check(L.tds_workspace_bytes(ctypes.byref(d), ctypes.byref(nb)))
+            _check(L.tds_batch_workspace_bytes(descs, count, ctypes.byref(nb)))
             self._ws = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device="cuda")
             base = self._ws.data_ptr()
             ws_ptr = (base + 255) & ~255
             ws_bytes = int(nb.value)
         h = ctypes.c_void_p()
-        _check(L.tds_create_scene(ctypes.byref(d), ws_ptr, ws_bytes,
-                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        if count == 1:
+            _check(L.tds_create_scene(ctypes.byref(descs[0]), ws_ptr, ws_bytes,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        else:
+            _check(L.tds_create_batch(descs, count, ws_ptr, ws_bytes,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
-        if "tool" in s and s["tool"] is not None:
-            self.set_tool_pose(s["tool"])
 
     # -- calls ---------------------------------------------------------------
     def set_tool_pose(self, tool: dict):
@@ -296,6 +330,10 @@ class Scene:
     def set_recording(self, enable: bool = True):
         _check(lib().tds_set_recording(self.h, int(enable)))
 
+    def set_graph(self, enable: bool = True):
+        """Replay each step from a CUDA graph (needs a non-default stream)."""
+        _check(lib().tds_set_graph(self.h, int(enable)))
+
     def read_training_samples(self) -> dict:
         """Features (m, 10), targets (m, 3) and keys of the last recorded step,
         sorted by key."""
@@ -322,6 +360,51 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Scene):
+    """Independent scenes advanced together by the same launches: each scene
+    keeps its particles, heightfield, walls, tool and friction coefficients
+    and steps exactly as it would alone. Particle ids are global (scene q owns
+    ``offsets[q]:offsets[q + 1]``)."""
+
+    def __init__(self, scenes, stream=None, workspace: str = "torch",
+                 contacts_per_particle: int = 0, domains=None):
+        scenes = [dict(s) for s in scenes]
+        if domains is None:
+            domains = [None] * len(scenes)
+        self._create(scenes, stream, workspace, contacts_per_particle, domains)
+        for q, s in enumerate(scenes):
+            if s.get("tool") is not None:
+                self.set_scene_tool_pose(q, s["tool"])
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def set_scene_tool_pose(self, q: int, tool: dict):
+        _check(lib().tds_batch_set_tool_pose(self.h, int(q), _vec(tool["pos"], 3), _vec(tool["quat"], 4),
+                                             _vec(tool["vel"], 3), _vec(tool["angvel"], 3)))
+
+    def set_tool_poses(self, tools):
+        """Every scene's tool pose in one call (a sequence of pose dicts)."""
+        P = np.empty((len(self.sizes), 13), np.float32)
+        for q, t in enumerate(tools):
+            P[q, 0:3], P[q, 3:7], P[q, 7:10], P[q, 10:13] = t["pos"], t["quat"], t["vel"], t["angvel"]
+        _check(lib().tds_batch_set_tool_poses(self.h, ctypes.c_void_p(P.ctypes.data), len(self.sizes)))
+
+    def read_scene(self, q: int) -> dict:
+        """x, v, w of scene q as (n_q, 3) float32 arrays."""
+        n = self.sizes[q]
+        bufs = [np.empty(n, np.float32) for _ in range(9)]
+        ptrs = [ctypes.c_void_p(b.ctypes.data) for b in bufs]
+        _check(lib().tds_batch_read_particles(self.h, int(q), *ptrs, n))
+        return {"x": np.stack(bufs[0:3], 1), "v": np.stack(bufs[3:6], 1), "w": np.stack(bufs[6:9], 1)}
+
+    def read_tool_forces(self) -> np.ndarray:
+        """(scenes, 6) float64: force and torque on each scene's tool."""
+        out = np.zeros((len(self.sizes), 6), np.float32)
+        _check(lib().tds_batch_read_tool_forces(self.h, ctypes.c_void_p(out.ctypes.data), len(self.sizes)))
+        return out.astype(np.float64)
 
 
 # ---------------------------------------------------------------------------

@@ -78,3 +78,31 @@ def test_null_scene_calls_fail_cleanly(L):
     f = (ctypes.c_float * 3)()
     assert L.tds_read_tool_force(None, f, f) == -1
     L.tds_destroy_scene(None)
+
+
+def test_batch_descriptions_are_checked_on_the_host(L):
+    """A batch sizes its workspace from all scenes and refuses scenes whose
+    shared settings (step, material, solver) differ."""
+    import numpy as np
+    from paper_2011_00459_gb300 import tds
+    from tests.parity_cases import packed_scene
+
+    a, b = packed_scene(300, 1, iters=30), packed_scene(500, 2, iters=30)
+    da, ka, _ = tds._make_desc(a, 0, None)
+    db, kb, _ = tds._make_desc(b, 0, None)
+    arr = (tds.SceneDesc * 2)(da, db)
+    nb, n1, n2 = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    assert L.tds_batch_workspace_bytes(arr, 2, ctypes.byref(nb)) == 0
+    assert L.tds_workspace_bytes(ctypes.byref(da), ctypes.byref(n1)) == 0
+    assert L.tds_workspace_bytes(ctypes.byref(db), ctypes.byref(n2)) == 0
+    assert nb.value > max(n1.value, n2.value)
+    assert L.tds_batch_workspace_bytes(arr, 0, ctypes.byref(nb)) == -1
+    arr[1].dt = np.float32(1 / 120)
+    assert L.tds_batch_workspace_bytes(arr, 2, ctypes.byref(nb)) == -1
+    assert b"share" in L.tds_last_error()
+    arr[1].dt = arr[0].dt
+    arr[1].mu_t = 0.9  # friction may differ per scene
+    assert L.tds_batch_workspace_bytes(arr, 2, ctypes.byref(nb)) == 0
+    assert L.tds_set_graph(None, 1) == -1
+    assert L.tds_batch_set_tool_poses(None, None, 0) == -1
+    del ka, kb

@@ -1,0 +1,161 @@
+"""Batches of independent scenes and CUDA-graph replay on the GPU: every scene
+of a batch against the FP64 oracle (contact keys and colourings bit-exact,
+impulses within 1e-4, positions within 1e-6 m), every scene of a batch
+bitwise equal to the same scene stepped alone, and graph replay bitwise equal
+to kernel-by-kernel launches."""
+import numpy as np
+import pytest
+
+from paper_2011_00459_gb300 import scenes as S
+from tests.parity_cases import packed_scene, rel_impulse_error
+
+pytestmark = pytest.mark.gpu
+
+STATIC_BIT = 0x80000000
+
+
+@pytest.fixture(scope="module")
+def tds():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2011_00459_gb300 import build, tds
+
+    build.build()
+    return tds
+
+
+def scene_part(out, o, n):
+    """Contacts of the scene owning particle ids [o, o + n), keys made local."""
+    keys = out["keys"].astype(np.uint64)
+    a = (keys >> np.uint64(32)).astype(np.int64)
+    sel = (a >= o) & (a < o + n)
+    keys, lam, col = keys[sel], out["lam"][sel], out["colour"][sel]
+    b = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    pair = (b & STATIC_BIT) == 0
+    b = np.where(pair, b - o, b)
+    local = ((a[sel] - o).astype(np.uint64) << np.uint64(32)) | b.astype(np.uint64)
+    order = np.argsort(local, kind="stable")
+    return local[order], lam[order], col[order]
+
+
+def three_scenes():
+    """Overlapping in space on purpose (scenes must still never interact);
+    different sizes, friction, rolling resistance and tool poses."""
+    return [packed_scene(900, 31, mu_t=0.5, mu_r=0.1, iters=30),
+            packed_scene(1531, 32, mu_t=0.7, mu_r=0.2, iters=30),
+            packed_scene(617, 33, mu_t=0.9, mu_r=0.0, iters=30)]
+
+
+def moved(tool, k):
+    t = dict(tool)
+    t["pos"] = tuple(np.asarray(tool["pos"]) + np.asarray(tool["vel"]) * (k + 1) / 60.0)
+    return t
+
+
+def test_batch_scenes_match_oracle(tds, orc):
+    scenes = three_scenes()
+    b = tds.Batch(scenes)
+    b.step(1)
+    out = b.read_contacts()
+    st_all = b.stats()
+    for q, sc in enumerate(scenes):
+        st = orc.State(sc)
+        ref = orc.step(sc, st)
+        o, n = int(b.offsets[q]), b.sizes[q]
+        keys, lam, col = scene_part(out, o, n)
+        assert np.array_equal(keys, ref["keys"]), q
+        assert np.array_equal(col.astype(np.int64), ref["colour"].astype(np.int64)), q
+        assert rel_impulse_error(lam, ref["lam"]) <= 1e-4, q
+        parts = b.read_scene(q)
+        assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= 1e-6, q
+    assert st_all["n_contacts"] == len(out["keys"])
+    b.close()
+
+
+def test_batch_equals_scenes_run_alone(tds):
+    """Five steps with moving tools: positions and velocities bitwise equal,
+    tool forces equal up to the summation order."""
+    scenes = three_scenes()
+    steps = 5
+    b = tds.Batch(scenes)
+    for k in range(steps):
+        b.set_tool_poses([moved(s["tool"], k) for s in scenes])
+        b.step(1)
+    forces = b.read_tool_forces()
+    for q, sc in enumerate(scenes):
+        g = tds.Scene(sc)
+        for k in range(steps):
+            g.set_tool_pose(moved(sc["tool"], k))
+            g.step(1)
+        alone = g.read_particles()
+        f, t = g.read_tool_force()
+        g.close()
+        got = b.read_scene(q)
+        for key in ("x", "v", "w"):
+            assert np.array_equal(got[key], alone[key]), (q, key)
+        ft = np.concatenate([f, t])
+        assert np.abs(forces[q] - ft).max() <= 1e-5 * max(np.abs(ft).max(), 1e-3), q
+    b.close()
+
+
+def test_batch_rejects_mixed_settings(tds):
+    a = packed_scene(300, 1, iters=30)
+    c = packed_scene(300, 2, iters=40)
+    with pytest.raises(tds.TdsError):
+        tds.Batch([a, c])
+    d = packed_scene(300, 3, cohesion=0.0, iters=30)
+    with pytest.raises(tds.TdsError):
+        tds.Batch([a, d])
+
+
+def run_steps(tds, scene, graph, steps=8):
+    import torch
+
+    g = tds.Scene(scene, stream=torch.cuda.Stream())
+    g.set_graph(graph)
+    for k in range(steps):
+        if k == 4:
+            g.set_solver(40, 0.0, 10)  # settings change: the graph is captured again
+        g.set_tool_pose(moved(scene["tool"], k))
+        g.step(1)
+    parts = g.read_particles()
+    f, t = g.read_tool_force()
+    st = g.stats()
+    contacts = g.read_contacts()
+    g.close()
+    return parts, np.concatenate([f, t]), st, contacts
+
+
+def test_graph_replay_equals_launches(tds):
+    scene = packed_scene(1200, 41, iters=30)
+    p0, f0, s0, c0 = run_steps(tds, scene, False)
+    p1, f1, s1, c1 = run_steps(tds, scene, True)
+    for key in ("x", "v", "w"):
+        assert np.array_equal(p0[key], p1[key]), key
+    assert np.array_equal(c0["keys"], c1["keys"])
+    assert np.array_equal(c0["lam"], c1["lam"])
+    assert np.allclose(f0, f1, rtol=1e-6, atol=1e-6)
+    assert s0["kernel_launches"] == s1["kernel_launches"]
+
+
+def test_graph_replay_of_a_batch_in_residual_mode(tds):
+    """The batched workload's beds (small instances) settle under graph
+    replay with a residual target; the result equals plain launches."""
+    import torch
+
+    beds = S.batched(3, scenes=6, n_lo=800, n_hi=2500)
+    results = []
+    for graph in (False, True):
+        b = tds.Batch(beds, stream=torch.cuda.Stream())
+        b.set_graph(graph)
+        b.set_tool_poses([S.parked_tool(s) for s in beds])
+        b.set_solver(200, 1e-3, 10)
+        b.step(10)
+        results.append([b.read_scene(q)["x"] for q in range(len(beds))])
+        st = b.stats()
+        assert st["residual"] <= 1e-3 or st["iterations"] == 200
+        b.close()
+    for q in range(len(beds)):
+        assert np.array_equal(results[0][q], results[1][q]), q
