@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="tds", choices=["tds", "reference"])
     ap.add_argument("--workload", default="large")
     ap.add_argument("--n", type=int, default=0, help="override the particle count")
+    ap.add_argument("--scenes", type=int, default=0, help="batched workload: override the bed count")
+    ap.add_argument("--unbatched", action="store_true",
+                    help="batched workload: step the beds as separate scenes (the plain form)")
     ap.add_argument("--iters", type=int, default=0, help="override the sweeps per step")
     ap.add_argument("--settle", type=int, default=-1)
     ap.add_argument("--approach", type=float, default=0.3,
@@ -161,12 +164,7 @@ def ncu_traffic(workload: str) -> float | None:
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def make_workload(args, rank: int) -> dict:
-    from paper_2011_00459_gb300 import scenes as S
-
-    gen = S.WORKLOADS[args.workload]
-    kw = {"n": args.n} if args.n else {}
-    scene = gen(seed=args.seed + rank, **kw)
+def _apply_args(scene: dict, args) -> dict:
     if args.iters:
         scene["iters"] = args.iters
     if args.tol > 0:
@@ -178,7 +176,41 @@ def make_workload(args, rank: int) -> dict:
     return scene
 
 
-def describe(scene: dict, args) -> dict:
+def make_workload(args, rank: int):
+    """One scene dict, or for the batched workload a list of them."""
+    from paper_2011_00459_gb300 import scenes as S
+
+    if args.workload == "batched":
+        kw = {"scenes": args.scenes} if args.scenes else {}
+        return [_apply_args(s, args) for s in S.batched(seed=args.seed + rank, **kw)]
+    gen = S.WORKLOADS[args.workload]
+    kw = {"n": args.n} if args.n else {}
+    return _apply_args(gen(seed=args.seed + rank, **kw), args)
+
+
+def _solve_desc(scene: dict) -> str:
+    return (f"residual <= {scene['tol']:g} (cap {scene['iters']} sweeps)" if scene.get("tol", 0) > 0
+            else f"{scene['iters']} sweeps")
+
+
+def describe(work, args) -> dict:
+    if isinstance(work, list):
+        ns = np.array([len(s["r"]) for s in work])
+        s0 = work[0]
+        return {
+            "workload": f"batched: {len(work)} independent walled beds, {int(ns.sum())} spheres "
+                        f"(n per bed log-U[1e3, 2e4]: min {ns.min()}, mean {ns.mean():.0f}, max {ns.max()}), "
+                        f"r~U[0.03,0.05] m, 2:1 footprints 0.6 m deep, flat heightfields, blade speed "
+                        f"U[0.2,1.5] m/s, depth U[0.1,0.4] m, mu_t U[0.4,0.9], {_solve_desc(s0)} per step, "
+                        + ("each bed its own scene and launch sequence per step (unbatched)"
+                           if args.unbatched else
+                           "one launch sequence per step replayed from a CUDA graph"),
+            "particles": int(ns.sum()), "scenes": len(work), "sweeps": int(s0["iters"]), "dt": s0["dt"],
+            "solve": _solve_desc(s0),
+            "warm_start": "previous step" if s0.get("warm_start", 1) else "cold",
+            "seed": args.seed, "l2": "inputs larger than L2 (contact rows and impulses > 129 MB)",
+        }
+    scene = work
     return {
         "workload": f"{scene['name']}: {len(scene['r'])} spheres r~U[{scene['r'].min():.3f},"
                     f"{scene['r'].max():.3f}] m, {scene['footprint'][0]:g}x{scene['footprint'][1]:g} m "
@@ -186,38 +218,181 @@ def describe(scene: dict, args) -> dict:
                     f"{len(scene['tool_boxes'])}-box {scene['tool_kind']}, c_p {scene['cohesion']:g} Pa, "
                     f"{scene['iters']} PGS sweeps/step, previous-step warm start",
         "particles": int(len(scene["r"])), "sweeps": int(scene["iters"]), "dt": scene["dt"],
-        "solve": (f"residual <= {scene['tol']:g} (cap {scene['iters']} sweeps)" if scene.get("tol", 0) > 0
-                  else f"{scene['iters']} sweeps"),
+        "solve": _solve_desc(scene),
         "warm_start": "previous step" if scene.get("warm_start", 1) else "cold",
         "seed": args.seed, "l2": "inputs larger than L2 (contact rows and impulses > 129 MB)",
     }
 
 
-def settle_and_approach(g, scene, args, S):
-    """Untimed: settle the spawned bed with the tool parked, then move the
-    tool along its path up to the start of the timed region."""
-    settle = scene["settle_steps"] if args.settle < 0 else args.settle
-    g.set_tool_pose(S.parked_tool(scene))
-    g.set_solver(30)
-    for _ in range(settle):
-        g.step(1)
-    g.set_solver(int(scene["iters"]), float(scene.get("tol", 0.0)), int(scene.get("residual_every", 10)))
-    parts = g.read_particles()
-    surface = S.surface_level(parts["x"], scene["r"])
-    path = S.tool_path(scene, surface, seed=args.seed)
-    dt = scene["dt"]
-    length = getattr(path, "length", None)
-    t0 = 0.0
-    if length is not None:
-        t0 = args.approach * length / path.speed
-    else:
-        t0 = args.approach * path.push / path.speed
-    k = 0
-    while k * dt < t0:
-        g.set_tool_pose(path(k * dt))
-        g.step(1)
-        k += 1
-    return path, k, surface
+class PlainSim:
+    """One bed: settle with the tool parked, approach untimed, then dig."""
+
+    def __init__(self, tds, S, scene, stream, args):
+        self.g = tds.Scene(scene, stream=stream)
+        self.scene, self.S, self.args = scene, S, args
+        self.n = len(scene["r"])
+        self.dt = scene["dt"]
+
+    def settle_and_approach(self):
+        S, scene, args, g = self.S, self.scene, self.args, self.g
+        settle = scene["settle_steps"] if args.settle < 0 else args.settle
+        g.set_tool_pose(S.parked_tool(scene))
+        g.set_solver(30)
+        for _ in range(settle):
+            g.step(1)
+        g.set_solver(int(scene["iters"]), float(scene.get("tol", 0.0)), int(scene.get("residual_every", 10)))
+        parts = g.read_particles()
+        self.surface = S.surface_level(parts["x"], scene["r"])
+        self.path = S.tool_path(scene, self.surface, seed=args.seed)
+        length = getattr(self.path, "length", None)
+        t0 = args.approach * (length if length is not None else self.path.push) / self.path.speed
+        self.k = 0
+        while self.k * self.dt < t0:
+            self.advance()
+
+    def advance(self):
+        self.g.set_tool_pose(self.path(self.k * self.dt))
+        self.g.step(1)
+        self.k += 1
+
+    def read_back(self, xs):
+        self.g.read_positions_into(*xs)
+        self.g.read_tool_force()
+
+    def d2h_bytes(self):
+        return 3 * 4 * self.n + 6 * 4
+
+    def h2d_bytes(self):
+        return 13 * 4
+
+
+class BatchedSim(PlainSim):
+    """Independent beds in one batch, stepped by replayed CUDA graphs; every
+    bed settles with its blade parked, then all blades cut along their own
+    cycles (speed and depth per bed)."""
+
+    def __init__(self, tds, S, scenes, stream, args):
+        self.g = tds.Batch(scenes, stream=stream)
+        self.g.set_graph(True)
+        self.scenes, self.S, self.args = scenes, S, args
+        self.n = int(self.g.n)
+        self.dt = scenes[0]["dt"]
+
+    def settle_and_approach(self):
+        S, args, g = self.S, self.args, self.g
+        s0 = self.scenes[0]
+        settle = s0["settle_steps"] if args.settle < 0 else args.settle
+        g.set_tool_poses([S.parked_tool(s) for s in self.scenes])
+        g.set_solver(30)
+        g.step(settle)
+        g.set_solver(int(s0["iters"]), float(s0.get("tol", 0.0)), int(s0.get("residual_every", 10)))
+        self.paths = []
+        for q, s in enumerate(self.scenes):
+            surface = S.surface_level(g.read_scene(q)["x"], s["r"])
+            self.paths.append(S.tool_path(s, surface, seed=args.seed))
+        self.surface = float("nan")
+        self.k = 0
+        t0 = args.approach * float(np.median([p.push / p.speed for p in self.paths]))
+        while self.k * self.dt < t0:
+            self.advance()
+
+    def advance(self):
+        t = self.k * self.dt
+        self.g.set_tool_poses([p(t) for p in self.paths])
+        self.g.step(1)
+        self.k += 1
+
+    def read_back(self, xs):
+        self.g.read_positions_into(*xs)
+        self.g.read_tool_forces()
+
+    def d2h_bytes(self):
+        return 3 * 4 * self.n + 6 * 4 * len(self.scenes)
+
+    def h2d_bytes(self):
+        return 13 * 4 * len(self.scenes)
+
+
+class SceneGroup:
+    """Separate scenes on one stream, driven like one: the unbatched form of
+    a batch (each scene its own launch sequence every step)."""
+
+    def __init__(self, scenes):
+        self.scenes = scenes
+        self.n = sum(s.n for s in scenes)
+
+    def synchronize(self):
+        for s in self.scenes:
+            s.synchronize()
+
+    def set_timing(self, on=True):
+        for s in self.scenes:
+            s.set_timing(on)
+
+    def stats(self) -> dict:
+        out = None
+        for s in self.scenes:
+            st = s.stats()
+            if out is None:
+                out = st
+                out["n_colours"] = [st["n_colours"]]
+                out["colour_rounds"] = [st["colour_rounds"]]
+                out["residual"] = [st["residual"]]
+                continue
+            for k in ("n_contacts", "n_pp", "n_static", "kernel_launches", "sweep_contacts_pp",
+                      "sweep_contacts_static", "sum_contacts", "solved_steps"):
+                out[k] += st[k]
+            out["n_colours"].append(st["n_colours"])
+            out["colour_rounds"].append(st["colour_rounds"])
+            out["residual"].append(st["residual"])
+            for k in out["phase_ms"]:
+                out["phase_ms"][k] += st["phase_ms"][k]
+        out["n_colours"] = max(out["n_colours"])
+        out["colour_rounds"] = max(out["colour_rounds"])
+        out["residual"] = max(out["residual"])
+        out["solved_steps"] //= len(self.scenes)
+        return out
+
+    def close(self):
+        for s in self.scenes:
+            s.close()
+
+
+class UnbatchedSim(BatchedSim):
+    """The batch's beds settled and approached in the batch (untimed), then
+    stepped as separate scenes, one launch sequence per bed and step."""
+
+    def __init__(self, tds, S, scenes, stream, args):
+        super().__init__(tds, S, scenes, stream, args)
+        self.tds, self.stream = tds, stream
+
+    def settle_and_approach(self):
+        super().settle_and_approach()
+        parts = []
+        for q, s in enumerate(self.scenes):
+            st = self.g.read_scene(q)
+            sc = dict(s)
+            sc["x"], sc["v"], sc["w"] = st["x"], st["v"], st["w"]
+            sc["tool"] = self.paths[q](self.k * self.dt)
+            parts.append(sc)
+        self.g.close()
+        self.g = SceneGroup([self.tds.Scene(sc, stream=self.stream) for sc in parts])
+
+    def advance(self):
+        if not isinstance(self.g, SceneGroup):  # settling and approach run in the batch
+            return BatchedSim.advance(self)
+        t = self.k * self.dt
+        for p, g in zip(self.paths, self.g.scenes):
+            g.set_tool_pose(p(t))
+            g.step(1)
+        self.k += 1
+
+    def read_back(self, xs):
+        o = 0
+        for g in self.g.scenes:
+            g.read_positions_into(xs[0][o:o + g.n], xs[1][o:o + g.n], xs[2][o:o + g.n])
+            g.read_tool_force()
+            o += g.n
 
 
 def run_tds(args, rank: int, world: int, local_rank: int):
@@ -233,21 +408,22 @@ def run_tds(args, rank: int, world: int, local_rank: int):
     if world > 1:
         torch.distributed.barrier()
         B.build()
-    scene = make_workload(args, rank)
-    n = len(scene["r"])
+    work = make_workload(args, rank)
     stream = torch.cuda.Stream()
     t_setup = time.time()
     with torch.cuda.stream(stream):
-        g = tds.Scene(scene, stream=stream)
-        path, k, surface = settle_and_approach(g, scene, args, S)
-        dt = scene["dt"]
+        if isinstance(work, list):
+            sim = (UnbatchedSim if args.unbatched else BatchedSim)(tds, S, work, stream, args)
+        else:
+            sim = PlainSim(tds, S, work, stream, args)
+        n = sim.n
+        sim.settle_and_approach()
+        g = sim.g  # the unbatched form replaces the batch by separate scenes here
         for _ in range(args.warmup):
-            g.set_tool_pose(path(k * dt))
-            g.step(1)
-            k += 1
+            sim.advance()
         g.synchronize()
         g.stats()  # reset the accumulators
-        log(args, f"setup {time.time() - t_setup:.1f}s, surface {surface:.3f}")
+        log(args, f"setup {time.time() - t_setup:.1f}s, surface {sim.surface:.3f}")
         # ---- device-timed region ------------------------------------------------
         g.set_timing(True)
         clocks = Clocks(local_rank)
@@ -262,9 +438,7 @@ def run_tds(args, rank: int, world: int, local_rank: int):
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
-            g.set_tool_pose(path(k * dt))
-            g.step(1)
-            k += 1
+            sim.advance()
         e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
@@ -287,27 +461,24 @@ def run_tds(args, rank: int, world: int, local_rank: int):
         if not args.no_e2e:
             xs = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
             for _ in range(2):  # warm the read path
-                g.set_tool_pose(path(k * dt)); g.step(1); k += 1
-                g.read_positions_into(*xs); g.read_tool_force()
+                sim.advance()
+                sim.read_back(xs)
             if world > 1:
                 torch.distributed.barrier()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.steps):
-                g.set_tool_pose(path(k * dt))
-                g.step(1)
-                k += 1
-                g.read_positions_into(*xs)
-                g.read_tool_force()
+                sim.advance()
+                sim.read_back(xs)
             t_e2e = time.perf_counter() - t0
             if world > 1:
                 t = torch.tensor([t_e2e], device="cuda")
                 torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
                 t_e2e = float(t.item())
             e2e = {"value": n_all * args.steps / t_e2e, "unit": UNIT,
-                   "h2d_bytes_per_step": 13 * 4, "d2h_bytes_per_step": 3 * 4 * n + 6 * 4}
+                   "h2d_bytes_per_step": sim.h2d_bytes(), "d2h_bytes_per_step": sim.d2h_bytes()}
         g.close()
-    return scene, n_all, ms, st, launches, clk, e2e
+    return work, n_all, ms, st, launches, clk, e2e
 
 
 # ---------------------------------------------------------------------------
@@ -348,19 +519,29 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
     return n * k / el, desc, k
 
 
+def sample_scene(work) -> dict:
+    """The scene the oracle samples: the bed itself, or the batch's bed of
+    median size."""
+    if not isinstance(work, list):
+        return work
+    ns = [len(s["r"]) for s in work]
+    return work[int(np.argsort(ns)[len(ns) // 2])]
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return 0
     from oracle import oracle
 
     oracle.build()
-    scene = make_workload(args, 0)
+    work = make_workload(args, 0)
+    scene = sample_scene(work)
     steps = max(1, args.steps)
     val, desc, k = oracle_sample(scene, 0.0, args.seed, steps=steps)
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
            "n_gpus": args.gpus, "steps": k, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": describe(scene, args),
+           "config": describe(work, args),
            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": desc},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -379,7 +560,7 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    scene, n_all, ms, st, launches, clk, e2e = run_tds(args, rank, world, local_rank)
+    work, n_all, ms, st, launches, clk, e2e = run_tds(args, rank, world, local_rank)
     peaks = measured_peaks()
     pgs_ms = st["phase_ms"]["pgs"]
     alg_bytes = BYTES_PP * st["sweep_contacts_pp"] + BYTES_STATIC * st["sweep_contacts_static"]
@@ -392,7 +573,7 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**describe(scene, args), "parallelism": f"replicas{world}" if world > 1 else "single",
+        "config": {**describe(work, args), "parallelism": f"replicas{world}" if world > 1 else "single",
                    "contacts_per_step": st["sum_contacts"] / max(1, st["solved_steps"]),
                    "colours": st["n_colours"], "colour_rounds": st["colour_rounds"],
                    "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
@@ -410,7 +591,7 @@ def main():
         from oracle import oracle
 
         oracle.build()
-        val, desc, _ = oracle_sample(scene, args.cpu_seconds, args.seed)
+        val, desc, _ = oracle_sample(sample_scene(work), args.cpu_seconds, args.seed)
         result["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": desc}
     if rank == 0:

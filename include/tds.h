@@ -237,8 +237,9 @@ tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_
  * (0, the default). The graph is captured on the next step and captured
  * again whenever the warm start, recording or solver settings change; tool
  * poses need no capture. Results are identical either way. Needs a stream
- * created by the caller (not the legacy default stream). With graphs on,
- * per-phase timing reports the whole step as its first phase. */
+ * created by the caller (not the legacy default stream). Per-phase timing
+ * (tds_set_timing) works with graphs: the graph then carries the phase
+ * events. */
 tds_status tds_set_graph(tds_scene *s, int32_t enable);
 
 /* ---- learned warm start ------------------------------------------------------

@@ -109,19 +109,27 @@ struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
 // What a captured step depends on besides device memory: the kernel
 // arguments that the host settings select.
 struct GraphKey {
-  int use_prev = -1, warm = -1, recording = -1;
+  int use_prev = -1, warm = -1, recording = -1, timing = -1;
   uint32_t max_iters = 0, every = 0;
   float tol = -1.f;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording &&
-           max_iters == o.max_iters && every == o.every && tol == o.tol;
+           timing == o.timing && max_iters == o.max_iters && every == o.every && tol == o.tol;
   }
 };
 
 struct StepGraph {  // a captured step for one parity of the double buffers
+  cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   GraphKey key;
   uint64_t launches = 0;
+  cudaGraphNode_t ev_node[6] = {};  // phase-boundary event records (timing graphs)
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  }
 };
 
 }  // namespace
@@ -149,6 +157,7 @@ struct tds_scene {
   bool recording = false, have_weights = false;
   bool graph = false;
   StepGraph graphs[2];
+  cudaEvent_t graph_ev[6] = {};  // placeholders captured into timing graphs
   uint32_t parity = 0;
 };
 
@@ -615,23 +624,25 @@ tds_status set_pose_impl(tds_scene *s, uint32_t q, const float pos[3], const flo
   return TDS_OK;
 }
 
-// The kernels of one step, in order, on the scene's stream (capturable).
-tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches) {
+// The kernels of one step, in order, on the scene's stream (capturable:
+// under capture the phase events become event-record nodes of the graph).
+tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool capture = false) {
   DevPtrs &d = s->d;
   const tds_scene_desc &D = s->desc;
-  if (E) CUDA_TRY(cudaEventRecord(E[0], s->st));
+  const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[0], s->st, evf));
   launches += tds_launch_broadphase(d, s->k, s->L.ncells, s->st);
   std::swap(d.pos, d.pos2);
   std::swap(d.pv, d.pv2);
   std::swap(d.pid, d.pid2);
   std::swap(d.sid, d.sid2);
-  if (E) CUDA_TRY(cudaEventRecord(E[1], s->st));
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[1], s->st, evf));
   const bool learned = D.warm_start == TDS_WARM_LEARNED;
   // the learned warm start also reads the previous step's impulses
   int use_prev = (D.warm_start != TDS_WARM_COLD) && s->have_prev;
   launches += tds_launch_narrowphase(d, s->k, use_prev, s->st);
   launches += tds_launch_predict(d, s->k, s->st);
-  if (E) CUDA_TRY(cudaEventRecord(E[2], s->st));
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[2], s->st, evf));
   launches += tds_launch_colouring(d, s->L.n, s->L.cap, s->colour_blocks, 256, s->st);
   d.targ = s->recording ? s->x.targ : nullptr;
   if (learned || s->recording) launches += tds_launch_features(d, s->k, s->x.surf, s->L.ncols, s->L.cap, s->st);
@@ -640,13 +651,13 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches) {
     launches += 1;
   }
   launches += tds_launch_bucketing(d, s->L.cap, s->st);
-  if (E) CUDA_TRY(cudaEventRecord(E[3], s->st));
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[3], s->st, evf));
   CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned, s->pgs_blocks,
                           s->st));
   launches += 1;
-  if (E) CUDA_TRY(cudaEventRecord(E[4], s->st));
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[4], s->st, evf));
   launches += tds_launch_finish(d, s->k, s->L.cap, s->st);
-  if (E) CUDA_TRY(cudaEventRecord(E[5], s->st));
+  if (E) CUDA_TRY(cudaEventRecordWithFlags(E[5], s->st, evf));
   std::swap(d.prev_first[0], d.prev_first[1]);
   std::swap(d.prev_cnt[0], d.prev_cnt[1]);
   std::swap(d.prev_other[0], d.prev_other[1]);
@@ -663,42 +674,64 @@ GraphKey graph_key(const tds_scene *s) {
   g.max_iters = s->desc.max_iters;
   g.every = s->desc.residual_every;
   g.tol = s->desc.tol;
+  g.timing = s->timing;
   return g;
 }
 
 // One step replayed from a graph captured on first use (and again whenever
 // the settings it baked in change). Two graphs alternate because the step
-// swaps its double buffers; phase timing collapses to the whole step.
+// swaps its double buffers. With timing on, the graph holds event-record
+// nodes at the phase boundaries, pointed at this step's events before each
+// replay.
 tds_status step_graph(tds_scene *s, cudaEvent_t *E) {
   StepGraph &g = s->graphs[s->parity];
   const GraphKey key = graph_key(s);
   if (!g.exec || !(g.key == key)) {
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    g.exec = nullptr;
+    g.release();
+    if (E && !s->graph_ev[0])
+      for (int q = 0; q < 6; ++q) CUDA_TRY(cudaEventCreate(&s->graph_ev[q]));
     DevPtrs saved = s->d;
-    cudaGraph_t graph = nullptr;
     uint64_t launches = 0;
     CUDA_TRY(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal));
-    tds_status r = enqueue_step(s, nullptr, launches);
-    cudaError_t ce = cudaStreamEndCapture(s->st, &graph);
+    tds_status r = enqueue_step(s, E ? s->graph_ev : nullptr, launches, true);
+    cudaError_t ce = cudaStreamEndCapture(s->st, &g.graph);
     s->d = saved;  // enqueue_step swapped the buffers; the replay below swaps them
-    if (r != TDS_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return r;
+    if (r != TDS_OK || ce != cudaSuccess) {
+      g.release();
+      if (r != TDS_OK) return r;
+      return fail(TDS_ERR_CUDA, std::string("capturing the step: ") + cudaGetErrorString(ce));
     }
-    if (ce != cudaSuccess) return fail(TDS_ERR_CUDA, std::string("capturing the step: ") + cudaGetErrorString(ce));
-    ce = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) return fail(TDS_ERR_CUDA, std::string("instantiating the step: ") + cudaGetErrorString(ce));
+    if (E) {  // find the event-record nodes of the six phase boundaries
+      size_t nn = 0;
+      CUDA_TRY(cudaGraphGetNodes(g.graph, nullptr, &nn));
+      std::vector<cudaGraphNode_t> nodes(nn);
+      CUDA_TRY(cudaGraphGetNodes(g.graph, nodes.data(), &nn));
+      int found = 0;
+      for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev;
+        CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int q = 0; q < 6; ++q)
+          if (ev == s->graph_ev[q]) { g.ev_node[q] = nd; ++found; }
+      }
+      if (found != 6) {
+        g.release();
+        return fail(TDS_ERR_CUDA, "timing graph: phase events not found");
+      }
+    }
+    ce = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (ce != cudaSuccess) {
+      g.release();
+      return fail(TDS_ERR_CUDA, std::string("instantiating the step: ") + cudaGetErrorString(ce));
+    }
     g.key = key;
     g.launches = launches;
   }
-  if (E) CUDA_TRY(cudaEventRecord(E[0], s->st));
+  if (E)
+    for (int q = 0; q < 6; ++q) CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev_node[q], E[q]));
   CUDA_TRY(cudaGraphLaunch(g.exec, s->st));
-  if (E) {
-    for (int q = 1; q < 5; ++q) CUDA_TRY(cudaEventRecord(E[q], s->st));
-    CUDA_TRY(cudaEventRecord(E[5], s->st));
-  }
   s->launches += g.launches;
   DevPtrs &d = s->d;  // the same swaps as the captured step
   std::swap(d.pos, d.pos2);
@@ -1042,8 +1075,9 @@ void tds_destroy_scene(tds_scene *s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   else cudaDeviceSynchronize();
-  for (StepGraph &g : s->graphs)
-    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (StepGraph &g : s->graphs) g.release();
+  for (cudaEvent_t e : s->graph_ev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (s->owns && s->mem) cudaFree(s->mem);
   delete s;

@@ -159,3 +159,29 @@ def test_graph_replay_of_a_batch_in_residual_mode(tds):
         b.close()
     for q in range(len(beds)):
         assert np.array_equal(results[0][q], results[1][q]), q
+
+
+def test_phase_timing_under_graph_replay(tds):
+    """The graph carries the phase events: every phase gets a time and the
+    phases add up to the step."""
+    import torch
+
+    scene = packed_scene(1500, 42, iters=30)
+    g = tds.Scene(scene, stream=torch.cuda.Stream())
+    g.set_graph(True)
+    g.step(2)
+    g.stats()
+    g.set_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(4)
+    e1.record(g.stream)
+    st = g.stats()
+    torch.cuda.synchronize()
+    total = e0.elapsed_time(e1)
+    g.close()
+    assert st["timed_steps"] == 4
+    ph = st["phase_ms"]
+    assert all(v > 0 for v in ph.values()), ph
+    assert ph["pgs"] > ph["broadphase"]
+    assert sum(ph.values()) <= total * 1.01 + 0.05
