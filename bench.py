@@ -2,18 +2,23 @@
 
 Default workload: the 1 000 000-sphere excavation bed (r ~ U[0.02, 0.03] m,
 8 x 8 m, 1024^2 heightfield, 12-box bucket on a seeded spline dig, c_p 5 kPa,
-100 PGS sweeps per step, previous-step warm start). The bed is spawned on a
-jittered lattice and settled untimed on the GPU; the bucket then approaches
-its deepest cut untimed, and the timed steps dig.
+previous-step warm start), each step's PGS solved to the 1e-4 residual (cap
+2000 sweeps, checked every 5). The bed is spawned on a jittered lattice and
+settled untimed on the GPU; the bucket then approaches its deepest cut
+untimed, and the timed steps dig. ``--workload batched`` times 256
+independent beds in one batch (graph replay); ``--unbatched`` the same beds
+as separate scenes.
 
   value   = particles x timed steps / device time of those steps (CUDA events
             on the scene's stream, state resident in HBM)
   e2e     = the same through the C ABI with host buffers: every step sets the
             tool pose from the host and reads positions and tool force back
             into pinned host memory
-  roofline: the persistent PGS kernel, algorithmic bytes (204 B per
-            particle-pair contact and 160 B per static contact per sweep)
-            over its CUDA-event time, against the measured HBM copy peak
+  fixed_sweeps / roofline: a second timed region on the same bed with the
+            workload's fixed sweep count (100 for the large bed); the
+            roofline is the persistent PGS kernel's algorithmic bytes (204 B
+            per particle-pair contact and 160 B per static contact per sweep)
+            over its CUDA-event time there, against the measured HBM copy peak
   cpu_baseline: the FP64 CPU oracle on a bounded column of the same bed
 
 ``--impl reference`` times the oracle alone (the slow baseline arm).
@@ -60,8 +65,11 @@ def parse():
     ap.add_argument("--approach", type=float, default=0.3,
                     help="fraction of the dig path covered untimed before timing")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--tol", type=float, default=0.0,
-                    help="residual mode: stop each step's solve at this residual (cap --max-iters)")
+    ap.add_argument("--tol", type=float, default=1e-4,
+                    help="stop each step's solve at this residual (cap --max-iters); 0: fixed sweeps")
+    ap.add_argument("--roofline-sweeps", type=int, default=-1,
+                    help="sweeps per step of the second timed region that gives the PGS roofline "
+                         "(-1: the workload's fixed sweep count, 0: no second region)")
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cold", action="store_true", help="cold start instead of previous-step impulses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -167,6 +175,7 @@ def ncu_traffic(workload: str) -> float | None:
 def _apply_args(scene: dict, args) -> dict:
     if args.iters:
         scene["iters"] = args.iters
+    scene["fixed_iters"] = int(scene["iters"] if args.roofline_sweeps < 0 else args.roofline_sweeps)
     if args.tol > 0:
         scene["tol"] = args.tol
         scene["iters"] = args.max_iters
@@ -201,11 +210,11 @@ def describe(work, args) -> dict:
             "workload": f"batched: {len(work)} independent walled beds, {int(ns.sum())} spheres "
                         f"(n per bed log-U[1e3, 2e4]: min {ns.min()}, mean {ns.mean():.0f}, max {ns.max()}), "
                         f"r~U[0.03,0.05] m, 2:1 footprints 0.6 m deep, flat heightfields, blade speed "
-                        f"U[0.2,1.5] m/s, depth U[0.1,0.4] m, mu_t U[0.4,0.9], {_solve_desc(s0)} per step, "
+                        f"U[0.2,1.5] m/s, depth U[0.1,0.4] m, mu_t U[0.4,0.9], PGS to {_solve_desc(s0)} per step, "
                         + ("each bed its own scene and launch sequence per step (unbatched)"
                            if args.unbatched else
                            "one launch sequence per step replayed from a CUDA graph"),
-            "particles": int(ns.sum()), "scenes": len(work), "sweeps": int(s0["iters"]), "dt": s0["dt"],
+            "particles": int(ns.sum()), "scenes": len(work), "max_sweeps": int(s0["iters"]), "dt": s0["dt"],
             "solve": _solve_desc(s0),
             "warm_start": "previous step" if s0.get("warm_start", 1) else "cold",
             "seed": args.seed, "l2": "inputs larger than L2 (contact rows and impulses > 129 MB)",
@@ -216,8 +225,8 @@ def describe(work, args) -> dict:
                     f"{scene['r'].max():.3f}] m, {scene['footprint'][0]:g}x{scene['footprint'][1]:g} m "
                     f"walled bed, {scene['hf']['nx']}x{scene['hf']['ny']} heightfield, "
                     f"{len(scene['tool_boxes'])}-box {scene['tool_kind']}, c_p {scene['cohesion']:g} Pa, "
-                    f"{scene['iters']} PGS sweeps/step, previous-step warm start",
-        "particles": int(len(scene["r"])), "sweeps": int(scene["iters"]), "dt": scene["dt"],
+                    f"PGS to {_solve_desc(scene)} per step, previous-step warm start",
+        "particles": int(len(scene["r"])), "max_sweeps": int(scene["iters"]), "dt": scene["dt"],
         "solve": _solve_desc(scene),
         "warm_start": "previous step" if scene.get("warm_start", 1) else "cold",
         "seed": args.seed, "l2": "inputs larger than L2 (contact rows and impulses > 129 MB)",
@@ -328,6 +337,10 @@ class SceneGroup:
     def set_timing(self, on=True):
         for s in self.scenes:
             s.set_timing(on)
+
+    def set_solver(self, iters, tol=0.0, every=10):
+        for s in self.scenes:
+            s.set_solver(iters, tol, every)
 
     def stats(self) -> dict:
         out = None
@@ -477,8 +490,34 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                 t_e2e = float(t.item())
             e2e = {"value": n_all * args.steps / t_e2e, "unit": UNIT,
                    "h2d_bytes_per_step": sim.h2d_bytes(), "d2h_bytes_per_step": sim.d2h_bytes()}
+        # ---- fixed sweeps (the roofline region), same bed continuing its dig ----
+        fixed = None
+        first = work[0] if isinstance(work, list) else work
+        if first.get("tol", 0) > 0 and first["fixed_iters"] > 0:
+            g.set_solver(int(first["fixed_iters"]), 0.0, 10)
+            for _ in range(2):
+                sim.advance()
+            g.synchronize()
+            g.stats()
+            g.set_timing(True)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                sim.advance()
+            f1.record(stream)
+            torch.cuda.synchronize()
+            fms = f0.elapsed_time(f1)
+            fst = g.stats()
+            g.set_timing(False)
+            if world > 1:
+                t = torch.tensor([fms], device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                fms = float(t.item())
+            fixed = {"ms": fms, "st": fst, "sweeps": int(first["fixed_iters"])}
         g.close()
-    return work, n_all, ms, st, launches, clk, e2e
+    return work, n_all, ms, st, launches, clk, e2e, fixed
 
 
 # ---------------------------------------------------------------------------
@@ -515,7 +554,7 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
         if (steps is not None and k >= steps) or (steps is None and el >= seconds):
             break
     desc = (f"FP64 oracle, 1 thread: {n}-sphere column (0.5x0.5 m footprint) of the same bed, "
-            f"oracle-settled 60 steps untimed, then {k} steps of {scene['iters']} sweeps timed")
+            f"oracle-settled 60 steps untimed, then {k} steps timed, PGS to {_solve_desc(scene)}")
     return n * k / el, desc, k
 
 
@@ -560,14 +599,18 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    work, n_all, ms, st, launches, clk, e2e = run_tds(args, rank, world, local_rank)
+    work, n_all, ms, st, launches, clk, e2e, fixed = run_tds(args, rank, world, local_rank)
     peaks = measured_peaks()
-    pgs_ms = st["phase_ms"]["pgs"]
-    alg_bytes = BYTES_PP * st["sweep_contacts_pp"] + BYTES_STATIC * st["sweep_contacts_static"]
+    # roofline of k_pgs: over the fixed-sweep region when there is one (every
+    # launch then does the same sweeps), else over the headline region
+    rst = fixed["st"] if fixed else st
+    pgs_ms = rst["phase_ms"]["pgs"]
+    alg_bytes = BYTES_PP * rst["sweep_contacts_pp"] + BYTES_STATIC * rst["sweep_contacts_static"]
     achieved = alg_bytes / (pgs_ms * 1e-3) / 1e9 if pgs_ms > 0 else 0.0
     per = ncu_traffic(args.workload)
-    sweeps_contacts = st["sweep_contacts_pp"] + st["sweep_contacts_static"]
-    traffic = per * sweeps_contacts / max(1, st["solved_steps"]) if per is not None else None
+    sweeps_contacts = rst["sweep_contacts_pp"] + rst["sweep_contacts_static"]
+    traffic = per * sweeps_contacts / max(1, rst["solved_steps"]) if per is not None else None
+    phase = lambda q: {k: v / max(1, q["timed_steps"]) for k, v in q["phase_ms"].items()}
     result = {
         "metric": METRIC, "value": n_all * args.steps / (ms * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -578,15 +621,24 @@ def main():
                    "colours": st["n_colours"], "colour_rounds": st["colour_rounds"],
                    "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
                    "final_residual": st["residual"],
-                   "phase_ms_per_step": {k: v / max(1, st["timed_steps"]) for k, v in st["phase_ms"].items()}},
+                   "phase_ms_per_step": phase(st)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "kernel": "k_pgs (persistent colour-sweep PGS)",
+                     "region": (f"second timed region: {fixed['sweeps']} fixed sweeps per step, {args.steps} "
+                                f"steps of the same bed continuing its dig" if fixed else "the headline region"),
                      "peak_source": peaks["source"] + " HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": e2e,
     }
+    if fixed:
+        fs = fixed["st"]
+        result["fixed_sweeps"] = {
+            "sweeps": fixed["sweeps"], "value": n_all * args.steps / (fixed["ms"] * 1e-3), "unit": UNIT,
+            "ms_per_step": fixed["ms"] / args.steps,
+            "contacts_per_step": fs["sum_contacts"] / max(1, fs["solved_steps"]),
+            "phase_ms_per_step": phase(fs)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
 
