@@ -45,6 +45,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s at fixed PGS residual; plain vs batched/learned on 1 GB300"
 UNIT = "particle-steps/s"
+SETTLE_SWEEPS = 30   # PGS sweeps per untimed settle step
+TUNE_RESERVE = 80    # last settle steps available to the launch-shape autotuner
 BYTES_PP = 204.0      # per particle-pair contact per sweep
 BYTES_STATIC = 160.0  # per static contact per sweep
 
@@ -58,6 +60,11 @@ def parse():
     ap.add_argument("--workload", default="large")
     ap.add_argument("--n", type=int, default=0, help="override the particle count")
     ap.add_argument("--scenes", type=int, default=0, help="batched workload: override the bed count")
+    ap.add_argument("--pgs-sync", type=int, default=-1, choices=[-1, 0, 1],
+                    help="solver sync between colours: 1 neighbour, 0 grid barrier (-1: library default)")
+    ap.add_argument("--pgs-blocks", type=int, default=0, help="solver CTAs (0: library default)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shapes (no untimed tuning before warm-up)")
     ap.add_argument("--unbatched", action="store_true",
                     help="batched workload: step the beds as separate scenes (the plain form)")
     ap.add_argument("--iters", type=int, default=0, help="override the sweeps per step")
@@ -242,13 +249,18 @@ class PlainSim:
         self.n = len(scene["r"])
         self.dt = scene["dt"]
 
-    def settle_and_approach(self):
+    def settle_and_approach(self, between=None):
         S, scene, args, g = self.S, self.scene, self.args, self.g
         settle = scene["settle_steps"] if args.settle < 0 else args.settle
         g.set_tool_pose(S.parked_tool(scene))
-        g.set_solver(30)
-        for _ in range(settle):
-            g.step(1)
+        g.set_solver(SETTLE_SWEEPS)
+        reserve = min(settle, TUNE_RESERVE)
+        g.step(settle - reserve)
+        # the last settle steps host the launch-shape choice: its timed steps
+        # are settle steps (same sweeps, tool parked) and launch shapes do not
+        # change results, so the trajectory is the one an untuned run takes
+        taken = between() if between else 0
+        g.step(max(0, reserve - taken))
         g.set_solver(int(scene["iters"]), float(scene.get("tol", 0.0)), int(scene.get("residual_every", 10)))
         parts = g.read_particles()
         self.surface = S.surface_level(parts["x"], scene["r"])
@@ -287,13 +299,16 @@ class BatchedSim(PlainSim):
         self.n = int(self.g.n)
         self.dt = scenes[0]["dt"]
 
-    def settle_and_approach(self):
+    def settle_and_approach(self, between=None):
         S, args, g = self.S, self.args, self.g
         s0 = self.scenes[0]
         settle = s0["settle_steps"] if args.settle < 0 else args.settle
         g.set_tool_poses([S.parked_tool(s) for s in self.scenes])
-        g.set_solver(30)
-        g.step(settle)
+        g.set_solver(SETTLE_SWEEPS)
+        reserve = min(settle, TUNE_RESERVE)
+        g.step(settle - reserve)
+        taken = between() if between else 0  # launch shapes chosen on settle steps (see PlainSim)
+        g.step(max(0, reserve - taken))
         g.set_solver(int(s0["iters"]), float(s0.get("tol", 0.0)), int(s0.get("residual_every", 10)))
         self.paths = []
         for q, s in enumerate(self.scenes):
@@ -379,8 +394,8 @@ class UnbatchedSim(BatchedSim):
         super().__init__(tds, S, scenes, stream, args)
         self.tds, self.stream = tds, stream
 
-    def settle_and_approach(self):
-        super().settle_and_approach()
+    def settle_and_approach(self, between=None):
+        super().settle_and_approach(None)  # the separate scenes keep the default shapes
         parts = []
         for q, s in enumerate(self.scenes):
             st = self.g.read_scene(q)
@@ -408,6 +423,52 @@ class UnbatchedSim(BatchedSim):
             o += g.n
 
 
+class _Parked:
+    """A sim whose steps keep the tools where they are (parked): what the
+    autotuner steps while it times launch shapes."""
+
+    def __init__(self, sim):
+        self.g = sim.g
+
+    def advance(self):
+        self.g.step(1)
+
+
+def prepare(args, work, tds, S, stream, replay=None):
+    """Creates the sim, settles it, picks the launch shapes (autotuned on the
+    settled bed, tools parked; or ``replay``'s shape with the same number of
+    parked steps, so the trajectory repeats), approaches and warms up."""
+    if isinstance(work, list):
+        sim = (UnbatchedSim if args.unbatched else BatchedSim)(tds, S, work, stream, args)
+    else:
+        sim = PlainSim(tds, S, work, stream, args)
+    tuned = {}
+
+    def between() -> int:
+        """Sets the launch shapes during the settle; returns the settle steps taken."""
+        g = sim.g
+        if args.pgs_sync >= 0 or args.pgs_blocks:
+            g.set_launch_config(pgs_blocks=args.pgs_blocks, pgs_sync=None if args.pgs_sync < 0 else args.pgs_sync)
+        elif replay is not None:
+            g.set_launch_config(**replay["shape"])
+            tuned.update(replay)
+        elif not args.no_autotune:
+            from paper_2011_00459_gb300 import autotune
+
+            tuned.update(autotune.tune(_Parked(sim), sweeps=SETTLE_SWEEPS, use_cache=False,
+                                       log=lambda m: log(args, m)))
+            log(args, f"autotune: {tuned}")
+            return int(tuned["steps"])
+        return 0
+
+    sim.settle_and_approach(between)
+    for _ in range(args.warmup):
+        sim.advance()
+    sim.g.synchronize()
+    sim.g.stats()  # reset the accumulators
+    return sim, (tuned or None)
+
+
 def run_tds(args, rank: int, world: int, local_rank: int):
     import torch
 
@@ -422,20 +483,12 @@ def run_tds(args, rank: int, world: int, local_rank: int):
         torch.distributed.barrier()
         B.build()
     work = make_workload(args, rank)
+    first = work[0] if isinstance(work, list) else work
     stream = torch.cuda.Stream()
     t_setup = time.time()
     with torch.cuda.stream(stream):
-        if isinstance(work, list):
-            sim = (UnbatchedSim if args.unbatched else BatchedSim)(tds, S, work, stream, args)
-        else:
-            sim = PlainSim(tds, S, work, stream, args)
-        n = sim.n
-        sim.settle_and_approach()
-        g = sim.g  # the unbatched form replaces the batch by separate scenes here
-        for _ in range(args.warmup):
-            sim.advance()
-        g.synchronize()
-        g.stats()  # reset the accumulators
+        sim, tuned = prepare(args, work, tds, S, stream)
+        g, n = sim.g, sim.n
         log(args, f"setup {time.time() - t_setup:.1f}s, surface {sim.surface:.3f}")
         # ---- device-timed region ------------------------------------------------
         g.set_timing(True)
@@ -469,30 +522,8 @@ def run_tds(args, rank: int, world: int, local_rank: int):
         else:
             n_all = float(n)
         g.set_timing(False)
-        # ---- end-to-end through the C ABI with host buffers ---------------------
-        e2e = None
-        if not args.no_e2e:
-            xs = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
-            for _ in range(2):  # warm the read path
-                sim.advance()
-                sim.read_back(xs)
-            if world > 1:
-                torch.distributed.barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                sim.advance()
-                sim.read_back(xs)
-            t_e2e = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([t_e2e], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                t_e2e = float(t.item())
-            e2e = {"value": n_all * args.steps / t_e2e, "unit": UNIT,
-                   "h2d_bytes_per_step": sim.h2d_bytes(), "d2h_bytes_per_step": sim.d2h_bytes()}
         # ---- fixed sweeps (the roofline region), same bed continuing its dig ----
         fixed = None
-        first = work[0] if isinstance(work, list) else work
         if first.get("tol", 0) > 0 and first["fixed_iters"] > 0:
             g.set_solver(int(first["fixed_iters"]), 0.0, 10)
             for _ in range(2):
@@ -516,8 +547,39 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                 torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
                 fms = float(t.item())
             fixed = {"ms": fms, "st": fst, "sweeps": int(first["fixed_iters"])}
+        one = g.scenes[0] if isinstance(g, SceneGroup) else g
+        launch_cfg = one.launch_config()
+        if tuned:
+            launch_cfg["autotune"] = {k: tuned[k] for k in ("source", "ms", "default_ms", "steps") if k in tuned}
         g.close()
-    return work, n_all, ms, st, launches, clk, e2e, fixed
+        # ---- end-to-end through the C ABI with host buffers ---------------------
+        # a second, identical preparation: the same settled bed, launch shapes,
+        # approach and warm-up, so the e2e loop times the same steps as above
+        e2e = None
+        if not args.no_e2e:
+            sim, _ = prepare(args, work, tds, S, stream, replay=tuned)
+            g = sim.g
+            xs = [torch.empty(n, dtype=torch.float32).pin_memory().numpy() for _ in range(3)]
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                sim.advance()
+                sim.read_back(xs)
+            t_e2e = time.perf_counter() - t0
+            est = g.stats()
+            if world > 1:
+                t = torch.tensor([t_e2e], device="cuda")
+                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+                t_e2e = float(t.item())
+            e2e = {"value": n_all * args.steps / t_e2e, "unit": UNIT,
+                   "h2d_bytes_per_step": sim.h2d_bytes(), "d2h_bytes_per_step": sim.d2h_bytes(),
+                   "mean_sweeps": (est["sweep_contacts_pp"] + est["sweep_contacts_static"])
+                   / max(1, est["sum_contacts"]),
+                   "steps": "the same steps as the device-timed region (identical preparation)"}
+            g.close()
+    return work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg
 
 
 # ---------------------------------------------------------------------------
@@ -599,7 +661,7 @@ def main():
 
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    work, n_all, ms, st, launches, clk, e2e, fixed = run_tds(args, rank, world, local_rank)
+    work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(args, rank, world, local_rank)
     peaks = measured_peaks()
     # roofline of k_pgs: over the fixed-sweep region when there is one (every
     # launch then does the same sweeps), else over the headline region
@@ -621,6 +683,7 @@ def main():
                    "colours": st["n_colours"], "colour_rounds": st["colour_rounds"],
                    "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
                    "final_residual": st["residual"],
+                   "launch": launch_cfg,
                    "phase_ms_per_step": phase(st)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,

@@ -242,6 +242,23 @@ tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_
  * events. */
 tds_status tds_set_graph(tds_scene *s, int32_t enable);
 
+/* ---- launch shapes ------------------------------------------------------------
+ * Knobs of the GPU schedule (the paper, a CPU method, has none). Results do
+ * not depend on them: every setting gives the same impulses and states bit
+ * for bit. pgs_blocks: persistent solver CTAs (one per SM at most);
+ * pgs_sync: between colours the solver either synchronises each CTA only
+ * with the CTAs whose particles it can touch (1, the default) or all CTAs
+ * with a grid barrier (0); colour_blocks: persistent colouring CTAs.
+ * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
+ * tds_set_launch_config ignores the max fields; a zero pgs_blocks or
+ * colour_blocks keeps the current value. */
+typedef struct {
+  int32_t pgs_blocks, pgs_sync, colour_blocks;
+  int32_t max_pgs_blocks, max_colour_blocks;
+} tds_launch_config;
+tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out);
+tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg);
+
 /* ---- learned warm start ------------------------------------------------------
  * Not in the paper, whose discussion proposes data-driven models trained on
  * resolved simulations as future work: a 10 -> 64 -> 64 -> 3 ReLU network

@@ -29,7 +29,7 @@ void tds_mlp_adam_launch(float *params, float *grad, float *mom, float *vel, uin
                          cudaStream_t st);
 int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
-                           uint32_t every, int apply_warm, int blocks, cudaStream_t st);
+                           uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st);
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 int tds_pgs_setup(int *threads);
@@ -110,11 +110,13 @@ struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
 // arguments that the host settings select.
 struct GraphKey {
   int use_prev = -1, warm = -1, recording = -1, timing = -1;
+  int pgs_blocks = -1, pgs_sync = -1, colour_blocks = -1;
   uint32_t max_iters = 0, every = 0;
   float tol = -1.f;
   bool operator==(const GraphKey &o) const {
-    return use_prev == o.use_prev && warm == o.warm && recording == o.recording &&
-           timing == o.timing && max_iters == o.max_iters && every == o.every && tol == o.tol;
+    return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
+           pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && colour_blocks == o.colour_blocks &&
+           max_iters == o.max_iters && every == o.every && tol == o.tol;
   }
 };
 
@@ -147,6 +149,8 @@ struct tds_scene {
   std::vector<BoxF> host_boxes;
   bool geo_dirty = true;
   int pgs_blocks = 1, colour_blocks = 1;
+  int pgs_sync = 1;       // solver: 1 neighbour synchronisation, 0 grid barrier
+  int max_pgs_blocks = 1, max_colour_blocks = 1;
   uint64_t steps = 0;
   tds_status latched = TDS_OK;
   uint64_t launches = 0;
@@ -367,6 +371,8 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   if (nd < 6 * 128) nd = 6 * 128;
   d.dpart = c.take<double>(nd);
   d.bar = c.take<uint32_t>(2);
+  d.prog = c.take<uint32_t>(kProgStride * (size_t)pgs_blocks);
+  d.rng = c.take<uint32_t>(2 * (size_t)pgs_blocks);
   size_t m = L.ncells;
   if (m < n) m = n;
   if (m < (size_t)TDS_NBUCKETS * L.ntiles) m = (size_t)TDS_NBUCKETS * L.ntiles;
@@ -510,6 +516,9 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
   }
   s->pgs_blocks = pgs_blocks_for(s->L.n, sms);  // one co-resident CTA per SM at most
   s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
+  s->max_pgs_blocks = sms * occ_pgs;
+  if (s->max_pgs_blocks > 64 * sms) s->max_pgs_blocks = 64 * sms;
+  s->max_colour_blocks = sms * occ_col;
   Carver probe{nullptr};
   DevPtrs tmp{};
   Extra tx;
@@ -653,7 +662,7 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool c
   launches += tds_launch_bucketing(d, s->L.cap, s->st);
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[3], s->st, evf));
   CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned, s->pgs_blocks,
-                          s->st));
+                          s->pgs_sync, s->st));
   launches += 1;
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[4], s->st, evf));
   launches += tds_launch_finish(d, s->k, s->L.cap, s->st);
@@ -675,6 +684,9 @@ GraphKey graph_key(const tds_scene *s) {
   g.every = s->desc.residual_every;
   g.tol = s->desc.tol;
   g.timing = s->timing;
+  g.pgs_blocks = s->pgs_blocks;
+  g.pgs_sync = s->pgs_sync;
+  g.colour_blocks = s->colour_blocks;
   return g;
 }
 
@@ -823,6 +835,28 @@ tds_status tds_set_warm_start(tds_scene *s, int32_t mode) {
   if (mode != TDS_WARM_COLD && mode != TDS_WARM_PREV && mode != TDS_WARM_LEARNED)
     return fail(TDS_ERR_INVALID_ARG, "unknown warm start");
   s->desc.warm_start = mode;
+  return TDS_OK;
+}
+
+tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out) {
+  if (!s || !out) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  out->pgs_blocks = s->pgs_blocks;
+  out->pgs_sync = s->pgs_sync;
+  out->colour_blocks = s->colour_blocks;
+  out->max_pgs_blocks = s->max_pgs_blocks;
+  out->max_colour_blocks = s->max_colour_blocks;
+  return TDS_OK;
+}
+
+tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
+  if (!s || !cfg) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (cfg->pgs_blocks < 0 || cfg->pgs_blocks > s->max_pgs_blocks || cfg->colour_blocks < 0 ||
+      cfg->colour_blocks > s->max_colour_blocks || (cfg->pgs_sync != 0 && cfg->pgs_sync != 1))
+    return fail(TDS_ERR_INVALID_ARG,
+                "pgs_blocks and colour_blocks must be in [0, max] (0 keeps the value), pgs_sync 0 or 1");
+  if (cfg->pgs_blocks) s->pgs_blocks = cfg->pgs_blocks;
+  if (cfg->colour_blocks) s->colour_blocks = cfg->colour_blocks;
+  s->pgs_sync = cfg->pgs_sync;
   return TDS_OK;
 }
 

@@ -5,8 +5,9 @@
 //     wider than any contact reach, count (atomics), scan (warp shuffles),
 //     scatter, sort each cell by particle id, and re-order the particle
 //     arrays by cell so that neighbours are contiguous in memory;
-//  2. narrowphase per owner particle (the one with the smaller id): the three
-//     contiguous rows of cells x 9 around it, the heightfield triangle under
+//  2. narrowphase per owner particle (the one with the smaller id): the 27
+//     cells around it as 9 runs of 3 cells contiguous along z (the fastest
+//     axis of the cell order), the heightfield triangle under
 //     it and every wall / tool box, each decided by the FP32 predicate below,
 //     which is bit-identical to the CPU oracle's (explicit round-to-nearest
 //     intrinsics, no FMA contraction);
@@ -106,14 +107,17 @@ __device__ __forceinline__ int cell_axis(float x, float x0, float inv, int n) {
 
 // Cell of a particle: its scene's block of gnx x gny x gnz cells, then the
 // cell inside it (coordinates clamped to the block, which keeps neighbouring
-// particles in neighbouring cells).
+// particles in neighbouring cells). z runs fastest, then y, then x: beds are
+// wide and shallow, so slot order walks vertical columns slab by slab and a
+// particle's neighbours lie within about one x-slab of it in slot order (the
+// solver's CTAs then touch only nearby slot ranges).
 __device__ __forceinline__ uint32_t cell_index(const StepConsts &k, const SceneGeo &G, uint32_t sid, float4 p,
                                                int &cx, int &cy, int &cz) {
   cx = cell_axis(p.x, G.lo[0], k.cell_inv, k.gnx);
   cy = cell_axis(p.y, G.lo[1], k.cell_inv, k.gny);
   cz = cell_axis(p.z, G.lo[2], k.cell_inv, k.gnz);
   const uint32_t cps = (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
-  return sid * cps + ((uint32_t)cz * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnx + (uint32_t)cx;
+  return sid * cps + ((uint32_t)cx * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnz + (uint32_t)cz;
 }
 
 // ---------------------------------------------------------------------------
@@ -174,11 +178,11 @@ __device__ __forceinline__ void for_each_contact(const DevPtrs &d, const StepCon
   int cx, cy, cz;
   (void)cell_index(k, G, sid, P, cx, cy, cz);
   const uint32_t block = sid * (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
-  const int x0 = max(cx - 1, 0), x1 = min(cx + 1, k.gnx - 1);
-  for (int z = max(cz - 1, 0); z <= min(cz + 1, k.gnz - 1); ++z) {
+  const int z0 = max(cz - 1, 0), z1 = min(cz + 1, k.gnz - 1);
+  for (int x = max(cx - 1, 0); x <= min(cx + 1, k.gnx - 1); ++x) {
     for (int y = max(cy - 1, 0); y <= min(cy + 1, k.gny - 1); ++y) {
-      uint32_t row = block + ((uint32_t)z * (uint32_t)k.gny + (uint32_t)y) * (uint32_t)k.gnx;
-      uint32_t s = __ldg(d.cell_start + row + x0), e = __ldg(d.cell_start + row + x1 + 1);
+      uint32_t row = block + ((uint32_t)x * (uint32_t)k.gny + (uint32_t)y) * (uint32_t)k.gnz;
+      uint32_t s = __ldg(d.cell_start + row + z0), e = __ldg(d.cell_start + row + z1 + 1);
       for (uint32_t j = s; j < e; ++j) {
         uint32_t pj = __ldg(d.pid + j);
         if (pj <= me) continue;

@@ -30,6 +30,8 @@ struct BoxF {
 // Geometry and material of one scene of a batch (device table; a single
 // scene is a batch of one). Scenes never touch: each has its own block of
 // broadphase cells, so its particles keep their own coordinates.
+constexpr uint32_t kProgStride = 32;  // words between the solver's progress flags
+
 struct SceneGeo {
   float lo[3];                 // origin of the scene's broadphase cells
   int hf_nx, hf_ny;            // heightfield (hf_nx == 0: none)
@@ -111,6 +113,9 @@ struct DevPtrs {
   float *fscal;               // see FS_* below
   double *dpart;              // per-block partial sums
   uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
+  uint32_t *prog;             // solver neighbour sync: last colour phase published per CTA,
+                              // one flag per kProgStride words (own 128-byte line)
+  uint32_t *rng;              // solver neighbour sync: touched slot range [lo, hi] per CTA
   uint32_t *scan_tmp;
   float *stage;               // 9 n floats for reads
   float *tool_out;            // 6 floats per scene

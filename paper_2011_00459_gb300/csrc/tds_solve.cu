@@ -188,6 +188,7 @@ struct SolveArgs {
   uint32_t max_iters, every;
   float tol, sig_t, sig_r;
   int apply_warm;
+  int sync;  // between colours: 0 grid barrier, 1 neighbour synchronisation
 };
 
 // ---------------------------------------------------------------------------
@@ -244,14 +245,58 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// This CTA's share [lo, hi) of colour col (its particle-pair bucket, padding,
-// then its static bucket), starting at a multiple of 4 contacts.
-__device__ __forceinline__ void colour_chunk(const DevPtrs &d, uint32_t col, uint32_t &lo, uint32_t &hi) {
-  const uint32_t s = d.bstart[2 * col], e = d.bend[2 * col + 1];
+// Segments: colour c has two, 2c (its particle-pair bucket) and 2c + 1 (its
+// static bucket). Each CTA takes the same share [lo, hi) of both, starting at
+// a multiple of 4 contacts, so its work in every colour lies in the same
+// stretch of slot order (buckets keep the owner order).
+__device__ __forceinline__ void seg_chunk(const DevPtrs &d, uint32_t g, uint32_t &lo, uint32_t &hi) {
+  const uint32_t s = d.bstart[g], e = d.bend[g];
   uint32_t q = (e - s + gridDim.x - 1) / gridDim.x;
   q = (q + 3u) & ~3u;
   lo = min(s + blockIdx.x * q, e);
   hi = min(lo + q, e);
+}
+
+// One wave of a colour: up to kWave contacts of this CTA's pair chunk
+// [lo1, hi1), then of its static chunk [lo2, hi2). The pair part n1 sits at
+// stage entries [0, n1), the static part n2 at [n1e, n1e + n2) with n1e = n1
+// rounded up to even (8-byte fields are copied in 16-byte pairs); n1e + n2 <=
+// kWave. Waves of a colour: the pair chunk in kWave pieces, the last one
+// topped up with static contacts, then the rest of the static chunk.
+struct WaveDesc {
+  uint32_t a1, n1, n1e, a2, n2;
+};
+
+__device__ __forceinline__ uint32_t waves_of(uint32_t L1, uint32_t L2) {
+  const uint32_t W1 = (L1 + kWave - 1) / kWave;
+  uint32_t first2 = 0;  // static contacts in the last pair wave
+  if (W1 > 0) {
+    const uint32_t n1 = L1 - (W1 - 1) * kWave;
+    first2 = min(L2, (uint32_t)kWave - ((n1 + 1u) & ~1u));
+  }
+  return W1 + (L2 - first2 + kWave - 1) / kWave;
+}
+
+__device__ __forceinline__ WaveDesc wave_desc(uint32_t lo1, uint32_t hi1, uint32_t lo2, uint32_t hi2, uint32_t w) {
+  const uint32_t L1 = hi1 - lo1, L2 = hi2 - lo2;
+  const uint32_t W1 = (L1 + kWave - 1) / kWave;
+  WaveDesc q{0, 0, 0, lo2, 0};
+  uint32_t first2 = 0;
+  if (W1 > 0) {
+    const uint32_t n1 = L1 - (W1 - 1) * kWave;
+    first2 = min(L2, (uint32_t)kWave - ((n1 + 1u) & ~1u));
+  }
+  if (w < W1) {
+    q.a1 = lo1 + w * kWave;
+    q.n1 = min((uint32_t)kWave, L1 - w * kWave);
+    q.n1e = (q.n1 + 1u) & ~1u;
+    if (w == W1 - 1) q.n2 = first2;
+  } else {
+    const uint32_t done = first2 + (w - W1) * kWave;
+    q.a2 = lo2 + done;
+    q.n2 = min((uint32_t)kWave, L2 - done);
+  }
+  return q;
 }
 
 // Walks the (sweep, colour, wave) sequence of this CTA's staged waves.
@@ -268,42 +313,102 @@ struct WaveSeq {
   }
 };
 
+__device__ __forceinline__ void stage_range(const DevPtrs &d, uint32_t p0, uint32_t cnt, uint32_t at,
+                                            unsigned char *stage, unsigned long long *bar) {
+  const uint32_t cnt2 = (cnt + 1u) & ~1u;  // 8-byte fields copied in pairs (16-byte multiples)
+  bulk_g2s(stage + kOffAb * kWave + 8u * at, d.p_ab + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffRn * kWave + 16u * at, d.p_rn + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRq * kWave + 16u * at, d.p_rq + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRm * kWave + 8u * at, d.p_rm + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffLa * kWave + 16u * at, d.p_la + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffLb * kWave + 8u * at, d.p_lb + p0, 8u * cnt2, bar);
+}
+
+__device__ __forceinline__ uint32_t range_bytes(uint32_t cnt) {
+  return cnt ? 3u * 16u * cnt + 3u * 8u * ((cnt + 1u) & ~1u) : 0u;
+}
+
 __device__ __forceinline__ void issue_wave(const DevPtrs &d, const WaveSeq &q, const uint32_t *lo,
                                            const uint32_t *hi, unsigned char *stage,
                                            unsigned long long *bar) {
-  const uint32_t p0 = lo[q.col] + q.w * kWave;
-  const uint32_t cnt = min((uint32_t)kWave, hi[q.col] - p0);
-  const uint32_t cnt2 = (cnt + 1u) & ~1u;  // 8-byte fields copied in pairs (16-byte multiples)
-  mbar_expect_tx(bar, 3u * 16u * cnt + 3u * 8u * cnt2);
-  bulk_g2s(stage + kOffAb * kWave, d.p_ab + p0, 8u * cnt2, bar);
-  bulk_g2s(stage + kOffRn * kWave, d.p_rn + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffRq * kWave, d.p_rq + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffRm * kWave, d.p_rm + p0, 8u * cnt2, bar);
-  bulk_g2s(stage + kOffLa * kWave, d.p_la + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffLb * kWave, d.p_lb + p0, 8u * cnt2, bar);
+  const WaveDesc w = wave_desc(lo[2 * q.col], hi[2 * q.col], lo[2 * q.col + 1], hi[2 * q.col + 1], q.w);
+  mbar_expect_tx(bar, range_bytes(w.n1) + range_bytes(w.n2));
+  if (w.n1) stage_range(d, w.a1, w.n1, 0, stage, bar);
+  if (w.n2) stage_range(d, w.a2, w.n2, w.n1e, stage, bar);
 }
 
-// The persistent solver: one CTA per SM, grid barrier between colours. The
-// rows and impulses of each wave (up to kWave contacts of one colour) are
-// staged in shared memory by bulk copies issued ahead, so they stream from
-// HBM while earlier colours are solved and barriers are crossed; each thread
-// then gathers both sides of its kPerThread contacts (through L2) before
-// solving any of them (contacts of one colour touch disjoint particles).
+// Neighbour synchronisation. Every CTA touches particles only inside its slot
+// range [rng_lo, rng_hi] (both sides of all its contacts, all colours); its
+// neighbours are the CTAs whose ranges overlap it (a symmetric relation).
+// Before colour phase t a CTA waits until each neighbour has published phase
+// t - 1; after its own stores of phase t it publishes t. Every write to a
+// particle before phase t then comes from a neighbour that has finished it,
+// and no neighbour can still be reading a particle this CTA writes, so the
+// result equals the grid-barrier order bit for bit. The least advanced CTA
+// never waits, so the scheme cannot deadlock. Each thread polls one
+// neighbour; waits are bounded like grid_barrier.
+__device__ __forceinline__ bool neighbour_wait(const DevPtrs &d, uint32_t jlo, uint32_t jhi, uint32_t target,
+                                               int *s_fail) {
+  const uint32_t j = jlo + threadIdx.x;
+  if (j <= jhi && j != blockIdx.x) {
+    unsigned long long t0 = 0;
+    for (unsigned spins = 0;; ++spins) {
+      uint32_t cur;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(d.prog + kProgStride * j) : "memory");
+      if ((int32_t)(cur - target) >= 0) break;
+      if ((spins & 31u) == 31u) {
+        if (*(volatile int32_t *)d.err != 0) { *s_fail = 1; break; }
+        unsigned long long t = global_ns();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > TDS_BARRIER_NS) {
+          latch_error(d.err, DEV_ERR_BARRIER);
+          *s_fail = 1;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return *s_fail == 0;
+}
+
+// Publishes phase t of this CTA; the caller has passed a __syncthreads after
+// the phase's stores (the release is cumulative over them).
+__device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
+  if (threadIdx.x == 0)
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(d.prog + kProgStride * blockIdx.x), "r"(t)
+                 : "memory");
+}
+
+// The persistent solver: one CTA per SM; between colours either a grid
+// barrier or neighbour synchronisation. The rows and impulses of each wave
+// (up to kWave contacts of one segment) are staged in shared memory by bulk
+// copies issued ahead, so they stream from HBM while earlier colours are
+// solved and synchronised; each thread then gathers both sides of its
+// kPerThread contacts (through L2) before solving any of them (contacts of
+// one colour touch disjoint particles).
 __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long full[kStages];
-  __shared__ uint32_t s_lo[TDS_MAX_COLOURS], s_hi[TDS_MAX_COLOURS], s_nw[TDS_MAX_COLOURS];
+  __shared__ uint32_t s_lo[2 * TDS_MAX_COLOURS], s_hi[2 * TDS_MAX_COLOURS], s_nw[TDS_MAX_COLOURS];
   __shared__ double sh[kPgsThreads / 32];
-  __shared__ int s_flag;
-  __shared__ uint32_t s_waves;
+  __shared__ uint32_t s_mn[kPgsThreads / 32], s_mx[kPgsThreads / 32];
+  __shared__ int s_flag, s_fail;
+  __shared__ uint32_t s_waves, s_jlo, s_jhi;
   const uint32_t ncol = min(d.ctr[CTR_NCOL], (uint32_t)TDS_MAX_COLOURS);
+  const uint32_t nseg = 2 * ncol;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t stride = gridDim.x * blockDim.x;
-  if (threadIdx.x == 0) s_waves = 0;
+  if (threadIdx.x == 0) {
+    s_waves = 0;
+    s_fail = 0;
+    s_jlo = s_jhi = blockIdx.x;
+  }
+  __syncthreads();
+  for (uint32_t g = threadIdx.x; g < nseg; g += blockDim.x) seg_chunk(d, g, s_lo[g], s_hi[g]);
   __syncthreads();
   for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
-    colour_chunk(d, c, s_lo[c], s_hi[c]);
-    s_nw[c] = (s_hi[c] - s_lo[c] + kWave - 1) / kWave;
+    s_nw[c] = waves_of(s_hi[2 * c] - s_lo[2 * c], s_hi[2 * c + 1] - s_lo[2 * c + 1]);
     atomicAdd(&s_waves, s_nw[c]);
   }
   if (threadIdx.x == 0) {
@@ -313,6 +418,52 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   __syncthreads();
   const uint32_t waves_per_sweep = s_waves;
   uint32_t gen = 0;  // grid barriers passed
+
+  if (a.sync) {  // this CTA's touched slot range, then its neighbours
+    uint32_t mn = 0xFFFFFFFFu, mx = 0u;
+    for (uint32_t g = 0; g < nseg; ++g)
+      for (uint32_t p = s_lo[g] + threadIdx.x; p < s_hi[g]; p += blockDim.x) {
+        const uint2 ab = __ldcg(d.p_ab + p);
+        if (ab.x == 0xFFFFFFFFu) continue;  // padding slot
+        mn = min(mn, ab.x);
+        mx = max(mx, ab.x);
+        if (is_dyn(ab.y)) {
+          mn = min(mn, ab.y);
+          mx = max(mx, ab.y);
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_mn[threadIdx.x >> 5] = mn;
+      s_mx[threadIdx.x >> 5] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kPgsThreads / 32; ++w) {
+        mn = min(mn, s_mn[w]);
+        mx = max(mx, s_mx[w]);
+      }
+      __stcg(d.rng + 2 * blockIdx.x, mn);
+      __stcg(d.rng + 2 * blockIdx.x + 1, mx);
+      s_mn[0] = mn;
+      s_mx[0] = mx;
+    }
+    if (!grid_barrier(d.bar, d.err, gen)) return;
+    const uint32_t lo = s_mn[0], hi = s_mx[0];
+    for (uint32_t j = threadIdx.x; j < gridDim.x; j += blockDim.x) {
+      const uint32_t jl = __ldcg(d.rng + 2 * j), jh = __ldcg(d.rng + 2 * j + 1);
+      if (lo <= hi && jl <= jh && max(lo, jl) <= min(hi, jh)) {
+        atomicMin(&s_jlo, j);
+        atomicMax(&s_jhi, j);
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t jlo = s_jlo, jhi = s_jhi;
   // staged impulses of a wave were written one sweep earlier by this CTA, so
   // never run further ahead than one sweep's worth of waves
   const uint32_t ahead = min((uint32_t)kStages, waves_per_sweep);
@@ -360,6 +511,9 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   float resid = -1.f;
   while (ok && it < a.max_iters) {
     for (uint32_t col = 0; col < ncol; ++col) {
+      const uint32_t phase = it * ncol + col + 1u;
+      const bool busy = s_nw[col] > 0;
+      if (a.sync && busy && !neighbour_wait(d, jlo, jhi, phase - 1u, &s_fail)) { ok = false; break; }
       for (uint32_t w = 0; w < s_nw[col]; ++w) {
         const uint32_t st = consumed % kStages;
         unsigned char *stage = smem + (size_t)st * kStageBytes;
@@ -370,26 +524,27 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         const float2 *srm = reinterpret_cast<const float2 *>(stage + kOffRm * kWave);
         const float4 *sla = reinterpret_cast<const float4 *>(stage + kOffLa * kWave);
         const float2 *slb = reinterpret_cast<const float2 *>(stage + kOffLb * kWave);
-        const uint32_t p0 = s_lo[col] + w * kWave;
-        const uint32_t cnt = min((uint32_t)kWave, s_hi[col] - p0);
+        const WaveDesc q = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], w);
         Side A[kPerThread], B[kPerThread];
+        uint32_t gp[kPerThread];  // colour-order index of each staged contact (or ~0)
         // gathers of every contact of this thread first (disjoint particles)
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
           const uint32_t li = j * kPgsThreads + threadIdx.x;
-          if (li < cnt) {
+          gp[j] = li < q.n1 ? q.a1 + li : (li >= q.n1e && li < q.n1e + q.n2 ? q.a2 + (li - q.n1e) : ~0u);
+          if (gp[j] != ~0u) {
             const uint2 ab = sab[li];
             if (ab.x != 0xFFFFFFFFu) {  // not a padding slot
               A[j] = load_side(d, ab.x);
               if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
-              else B[j] = Side{f3(d.p_sv[p0 + li]), f3(d.p_sw[p0 + li]), 0.f, 0.f};
+              else B[j] = Side{f3(d.p_sv[gp[j]]), f3(d.p_sw[gp[j]]), 0.f, 0.f};
             }
           }
         }
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
           const uint32_t li = j * kPgsThreads + threadIdx.x;
-          if (li < cnt) {
+          if (gp[j] != ~0u) {
             Row r;
             r.ab = sab[li];
             if (r.ab.x == 0xFFFFFFFFu) continue;
@@ -404,8 +559,8 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
             pgs_update(r, A[j], B[j], L0, L1, a.sig_t, a.sig_r);
             store_side(d, r.ab.x, A[j]);
             if (r.dyn) store_side(d, r.ab.y, B[j]);
-            d.p_la[p0 + li] = L0;
-            d.p_lb[p0 + li] = L1;
+            d.p_la[gp[j]] = L0;
+            d.p_lb[gp[j]] = L1;
           }
         }
         // impulses written above are read back by bulk copies one sweep later
@@ -420,11 +575,14 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         }
       }
       if (!ok) break;
-      if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
+      if (a.sync) publish(d, phase);
+      else if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
     }
     if (!ok) break;
     ++it;
     if (it == a.max_iters || (a.tol > 0.f && it % a.every == 0)) {
+      // the residual reads every contact: all colours of this sweep first
+      if (a.sync && !grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
       double num = 0.0, den = 0.0;
       for (uint32_t col = 0; col < ncol; ++col)
         for (int part = 0; part < 2; ++part)
@@ -602,9 +760,10 @@ int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
 }
 
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
-                           uint32_t every, int apply_warm, int blocks, cudaStream_t st) {
-  SolveArgs a{max_iters, every ? every : 1u, tol, k.sig_t, k.sig_r, apply_warm};
+                           uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st) {
+  SolveArgs a{max_iters, every ? every : 1u, tol, k.sig_t, k.sig_r, apply_warm, sync};
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
+  if (sync) cudaMemsetAsync(d.prog, 0, sizeof(uint32_t) * kProgStride * (size_t)blocks, st);
   DevPtrs dd = d;
   void *args[] = {&dd, &a};
   return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(kPgsThreads), args,

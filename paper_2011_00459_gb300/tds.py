@@ -31,7 +31,8 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_mlp_workspace_bytes", "tds_mlp_forward", "tds_mlp_loss_grad", "tds_mlp_adam_step",
             "tds_set_warm_start", "tds_batch_workspace_bytes", "tds_create_batch",
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
-            "tds_set_graph", "tds_batch_set_tool_poses"]
+            "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
+            "tds_set_launch_config"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -79,6 +80,12 @@ class StepStats(ctypes.Structure):
 PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
 
 
+class LaunchConfig(ctypes.Structure):
+    _fields_ = [("pgs_blocks", ctypes.c_int32), ("pgs_sync", ctypes.c_int32),
+                ("colour_blocks", ctypes.c_int32), ("max_pgs_blocks", ctypes.c_int32),
+                ("max_colour_blocks", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -124,6 +131,8 @@ def lib() -> ctypes.CDLL:
         L.tds_batch_read_tool_forces.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_set_graph.argtypes = [vp, ctypes.c_int32]
         L.tds_batch_set_tool_poses.argtypes = [vp, vp, ctypes.c_uint32]
+        L.tds_get_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
+        L.tds_set_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
         L.tds_destroy_scene.argtypes = [vp]
         L.tds_destroy_scene.restype = None
         L.tds_last_error.restype = ctypes.c_char_p
@@ -235,6 +244,7 @@ class Scene:
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
         self.n = int(self.offsets[-1])
         self.desc = descs[0]
+        self.solver = (int(descs[0].max_iters), float(descs[0].tol), int(descs[0].residual_every))
         self._descs = descs
         self._keep = keep
         L = lib()
@@ -316,6 +326,7 @@ class Scene:
 
     def set_solver(self, iters: int, tol: float = 0.0, residual_every: int = 10):
         _check(lib().tds_set_solver(self.h, int(iters), float(tol), int(residual_every)))
+        self.solver = (int(iters), float(tol), int(residual_every))
 
     def set_timing(self, enable: bool = True):
         _check(lib().tds_set_timing(self.h, int(enable)))
@@ -329,6 +340,21 @@ class Scene:
 
     def set_recording(self, enable: bool = True):
         _check(lib().tds_set_recording(self.h, int(enable)))
+
+    def launch_config(self) -> dict:
+        c = LaunchConfig()
+        _check(lib().tds_get_launch_config(self.h, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in LaunchConfig._fields_}
+
+    def set_launch_config(self, pgs_blocks: int = 0, pgs_sync: int | None = None, colour_blocks: int = 0):
+        """Solver CTAs, solver sync mode (1 neighbour, 0 grid barrier) and
+        colouring CTAs; 0 (or None for the mode) keeps the current value."""
+        c = LaunchConfig()
+        _check(lib().tds_get_launch_config(self.h, ctypes.byref(c)))
+        c.pgs_blocks, c.colour_blocks = int(pgs_blocks), int(colour_blocks)
+        if pgs_sync is not None:
+            c.pgs_sync = int(pgs_sync)
+        _check(lib().tds_set_launch_config(self.h, ctypes.byref(c)))
 
     def set_graph(self, enable: bool = True):
         """Replay each step from a CUDA graph (needs a non-default stream)."""

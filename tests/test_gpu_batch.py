@@ -185,3 +185,73 @@ def test_phase_timing_under_graph_replay(tds):
     assert all(v > 0 for v in ph.values()), ph
     assert ph["pgs"] > ph["broadphase"]
     assert sum(ph.values()) <= total * 1.01 + 0.05
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_launch_shapes_give_identical_results(tds, graph):
+    """Neighbour synchronisation vs grid barrier, fewer solver and colouring
+    CTAs: every launch shape gives the same states and impulses bit for bit
+    (a batch of uneven beds, moving tools, residual checks every 5 sweeps)."""
+    import torch
+
+    beds = S.batched(5, scenes=5, n_lo=800, n_hi=4000)
+    shapes = [dict(pgs_sync=1), dict(pgs_sync=0), dict(pgs_sync=1, pgs_blocks=7, colour_blocks=13),
+              dict(pgs_sync=0, pgs_blocks=3)]
+    out = []
+    for shape in shapes:
+        b = tds.Batch(beds, stream=torch.cuda.Stream())
+        b.set_graph(graph)
+        b.set_launch_config(**shape)
+        b.set_tool_poses([S.parked_tool(s) for s in beds])
+        b.set_solver(40, 1e-9, 5)
+        b.step(6)
+        paths = [S.tool_path(s, 0.3) for s in beds]
+        for k in range(4):
+            b.set_tool_poses([p(0.5 + k / 60.0) for p in paths])
+            b.step(1)
+        c = b.read_contacts()
+        x = [b.read_scene(q) for q in range(len(beds))]
+        cfg = b.launch_config()
+        b.close()
+        assert cfg["pgs_sync"] == shape["pgs_sync"]
+        out.append((c, x))
+    c0, x0 = out[0]
+    for c, x in out[1:]:
+        assert np.array_equal(c["keys"], c0["keys"])
+        assert np.array_equal(c["colour"], c0["colour"])
+        assert np.array_equal(c["lam"], c0["lam"])
+        for q in range(len(beds)):
+            for key in ("x", "v", "w"):
+                assert np.array_equal(x[q][key], x0[q][key]), (q, key)
+
+
+def test_autotuner_picks_a_candidate_and_caches_it(tds, tmp_path):
+    import torch
+
+    from paper_2011_00459_gb300 import autotune
+
+    beds = S.batched(6, scenes=4, n_lo=800, n_hi=3000)
+
+    class Sim:
+        def __init__(self):
+            self.g = tds.Batch(beds, stream=torch.cuda.Stream())
+            self.g.set_graph(True)
+            self.g.set_tool_poses([S.parked_tool(s) for s in beds])
+            self.g.set_solver(20, 1e-4, 5)
+            self.g.step(3)
+
+        def advance(self):
+            self.g.step(1)
+
+    path = str(tmp_path / "tune.json")
+    sim = Sim()
+    cfg0 = sim.g.launch_config()
+    r = autotune.tune(sim, steps=1, sweeps=10, path=path)
+    assert r["source"] == "timed"
+    assert r["shape"] in autotune.candidates(cfg0, torch.cuda.get_device_properties(0).multi_processor_count)
+    cfg = sim.g.launch_config()
+    assert {k: cfg[k] for k in r["shape"]} == r["shape"]
+    assert sim.g.solver == (20, 1e-4, 5)  # solver settings restored
+    again = autotune.tune(sim, path=path)
+    assert again["source"] == "cache" and again["shape"] == r["shape"]
+    sim.g.close()
