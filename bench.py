@@ -423,6 +423,34 @@ class UnbatchedSim(BatchedSim):
             o += g.n
 
 
+def time_aggregates(g, work, stream, reps: int) -> dict:
+    """Aggregate bodies of four zones per scene (quarters of each bed's
+    footprint, full height) on the current state: CUDA-event time per call
+    (kernels, the zone upload and the result read-back)."""
+    import torch
+
+    from paper_2011_00459_gb300 import scenes as S
+
+    beds = work if isinstance(work, list) else [work]
+    zones = []
+    for q, sc in enumerate(beds[:16]):
+        lx, ly = sc["footprint"]
+        for i in range(2):
+            for j in range(2):
+                zones.append({"scene": q, "planes": S.box_planes(((i + 0.5) * lx / 2, (j + 0.5) * ly / 2, 5.0),
+                                                                 (lx / 4, ly / 4, 10.0))})
+    out = g.aggregate_bodies(zones)  # warm
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        out = g.aggregate_bodies(zones)
+    e1.record(stream)
+    e1.synchronize()
+    return {"zones": len(zones), "particles_in_zones": int(sum(o["count"] for o in out)),
+            "ms_per_call": e0.elapsed_time(e1) / reps}
+
+
 class _Parked:
     """A sim whose steps keep the tools where they are (parked): what the
     autotuner steps while it times launch shapes."""
@@ -547,6 +575,9 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                 torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
                 fms = float(t.item())
             fixed = {"ms": fms, "st": fst, "sweeps": int(first["fixed_iters"])}
+        agg = None
+        if not isinstance(g, SceneGroup):
+            agg = time_aggregates(g, work, stream, args.steps)
         one = g.scenes[0] if isinstance(g, SceneGroup) else g
         launch_cfg = one.launch_config()
         if tuned:
@@ -579,6 +610,7 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                    / max(1, est["sum_contacts"]),
                    "steps": "the same steps as the device-timed region (identical preparation)"}
             g.close()
+    launch_cfg["aggregate_bodies"] = agg
     return work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg
 
 

@@ -242,6 +242,40 @@ tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_
  * events. */
 tds_status tds_set_graph(tds_scene *s, int32_t enable);
 
+/* ---- aggregate bodies ------------------------------------------------------------
+ * The coupling of the particles to the macroscale model (section "Macroscale
+ * model", Eqs. aggregate_mass to aggregate_rot_vel): the particles of each
+ * active zone are lumped into one rigid body with
+ *   M = sum m_a, x_A = sum m_a x_a / M, v_A = sum m_a v_a / M,
+ *   I_A = sum m_a (|x_a - x_A|^2 delta - (x_a - x_A)(x_a - x_A)^T),
+ *   omega_A = I_A^+ sum m_a (x_a - x_A) x v_a
+ * (the printed inertia is read as the point-mass tensor about the centre of
+ * mass; I_A^+ is the pseudo-inverse: no spin about an axis without inertia;
+ * voxels with fluidized mass are not part of this library).
+ * A zone is the intersection of 1..TDS_ZONE_MAX_PLANES half-spaces of one
+ * scene: a particle of that scene is inside iff, for every plane,
+ * (n_x x + n_y y) + n_z z <= d evaluated in FP32 in this order; it belongs to
+ * the first zone (in the given order) that contains it. Computed from the
+ * state after the last step on the scene's stream, accumulated in FP64.
+ * Waits. */
+#define TDS_MAX_ZONES 64
+#define TDS_ZONE_MAX_PLANES 8
+typedef struct {
+  uint32_t scene;     /* scene of the batch (0 for a single scene) */
+  uint32_t n_planes;  /* 1 .. TDS_ZONE_MAX_PLANES */
+  float planes[TDS_ZONE_MAX_PLANES][4];  /* (n_x, n_y, n_z, d) */
+} tds_zone;
+typedef struct {
+  uint32_t count;     /* particles in the zone (0: all fields zero) */
+  uint32_t pad;
+  double mass;        /* [kg] */
+  double com[3];      /* [m] */
+  double vel[3];      /* [m/s] */
+  double omega[3];    /* [rad/s] */
+  double inertia[6];  /* about com: xx, yy, zz, xy, xz, yz [kg m^2] */
+} tds_aggregate;
+tds_status tds_aggregate_bodies(tds_scene *s, const tds_zone *zones, uint32_t count, tds_aggregate *out);
+
 /* ---- launch shapes ------------------------------------------------------------
  * Knobs of the GPU schedule (the paper, a CPU method, has none). Results do
  * not depend on them: every setting gives the same impulses and states bit

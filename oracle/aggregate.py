@@ -69,16 +69,3 @@ def aggregate(x, v, r, density: float, zones, scene_of=None) -> list:
         omega = np.linalg.pinv(I, rcond=1e-12) @ L
         out.append({"count": int(sel.sum()), "mass": M, "com": com, "vel": vel, "inertia": I, "omega": omega})
     return out
-
-
-def box_planes(centre, half, R=np.eye(3)) -> np.ndarray:
-    """The 6 half-spaces of a box (centre, half extents, rotation R whose
-    columns are the box axes in world coordinates)."""
-    c = np.asarray(centre, np.float64)
-    out = []
-    for k in range(3):
-        axis = np.asarray(R, np.float64)[:, k]
-        for sgn in (1.0, -1.0):
-            nrm = sgn * axis
-            out.append([*nrm, float(nrm @ c + half[k])])
-    return np.asarray(out)

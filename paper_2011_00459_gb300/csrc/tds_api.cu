@@ -33,6 +33,9 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 int tds_pgs_setup(int *threads);
+int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, uint32_t nz, uint8_t *zone_id,
+                         double *sums, tds_aggregate *out, cudaStream_t st);
+size_t tds_aggregate_sums_words();
 const void *tds_colour_kernel();
 
 namespace {
@@ -97,6 +100,10 @@ struct Layout {
 };
 
 struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
+  tds_zone *zones = nullptr;       // aggregate bodies: zones, per-particle zone, sums, results
+  uint8_t *zone_id = nullptr;
+  double *agg_sums = nullptr;
+  tds_aggregate *agg_out = nullptr;
   float *heights = nullptr;
   SceneGeo *geo = nullptr;
   BoxF *boxes = nullptr;
@@ -388,6 +395,10 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   x.packed = c.take<unsigned char>(tds_mlp_packed_bytes());
   x.params = c.take<float>(tds_mlp_params());
   x.heights = c.take<float>(L.nheights);
+  x.zones = c.take<tds_zone>(TDS_MAX_ZONES);
+  x.zone_id = c.take<uint8_t>(n);
+  x.agg_sums = c.take<double>(tds_aggregate_sums_words());
+  x.agg_out = c.take<tds_aggregate>(TDS_MAX_ZONES);
   x.geo = c.take<SceneGeo>(L.S);
   x.boxes = c.take<BoxF>(L.nboxes);
   return c.off + 256;
@@ -1027,6 +1038,28 @@ tds_status tds_read_contacts(tds_scene *s, uint64_t *keys, float *lam, uint32_t 
       o[4] = l1[i].x; o[5] = l1[i].y; o[6] = l1[i].z;
     }
   return TDS_OK;
+}
+
+tds_status tds_aggregate_bodies(tds_scene *s, const tds_zone *zones, uint32_t count, tds_aggregate *out) {
+  if (!s || (count && (!zones || !out))) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (count > TDS_MAX_ZONES) return fail(TDS_ERR_INVALID_ARG, "more than TDS_MAX_ZONES zones");
+  for (uint32_t z = 0; z < count; ++z) {
+    if (zones[z].scene >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "zone scene out of range");
+    if (zones[z].n_planes < 1 || zones[z].n_planes > TDS_ZONE_MAX_PLANES)
+      return fail(TDS_ERR_INVALID_ARG, "zone needs 1..TDS_ZONE_MAX_PLANES planes");
+    for (uint32_t k = 0; k < zones[z].n_planes; ++k)
+      for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(zones[z].planes[k][q])) return fail(TDS_ERR_INVALID_ARG, "non-finite zone plane");
+  }
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  if (count == 0) return TDS_OK;
+  CUDA_TRY(cudaMemcpyAsync(s->x.zones, zones, sizeof(tds_zone) * count, cudaMemcpyHostToDevice, s->st));
+  s->launches += tds_launch_aggregate(s->d, s->L.n, s->x.zones, count, s->x.zone_id, s->x.agg_sums,
+                                      s->x.agg_out, s->st);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(out, s->x.agg_out, sizeof(tds_aggregate) * count, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
 }
 
 tds_status tds_set_mlp_weights(tds_scene *s, const float *params, uint32_t count) {

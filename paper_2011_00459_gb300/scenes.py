@@ -208,6 +208,19 @@ def bucket(width: float = 1.2, depth: float = 1.2, height: float = 0.9) -> np.nd
     return np.stack(boxes).astype(np.float32)
 
 
+def box_planes(centre, half, R=np.eye(3)) -> np.ndarray:
+    """A box as 6 half-spaces (n_x, n_y, n_z, d), inside iff n . x <= d
+    (centre, half extents, rotation R whose columns are the box axes)."""
+    c = np.asarray(centre, np.float64)
+    out = []
+    for k in range(3):
+        axis = np.asarray(R, np.float64)[:, k]
+        for sgn in (1.0, -1.0):
+            nrm = sgn * axis
+            out.append([*nrm, float(nrm @ c + half[k])])
+    return np.asarray(out, np.float32)
+
+
 def surface_level(x: np.ndarray, r: np.ndarray, q: float = 0.95) -> float:
     """Bed surface height: the q-quantile of z + r."""
     return float(np.quantile(np.asarray(x, np.float64)[:, 2] + np.asarray(r, np.float64), q))

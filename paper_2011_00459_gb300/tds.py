@@ -32,7 +32,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_warm_start", "tds_batch_workspace_bytes", "tds_create_batch",
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
-            "tds_set_launch_config"]
+            "tds_set_launch_config", "tds_aggregate_bodies"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -78,6 +78,20 @@ class StepStats(ctypes.Structure):
                 ("colour_rounds", ctypes.c_uint32)]
 
 PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
+
+
+MAX_ZONES, ZONE_MAX_PLANES = 64, 8
+
+
+class Zone(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_uint32), ("n_planes", ctypes.c_uint32),
+                ("planes", (ctypes.c_float * 4) * ZONE_MAX_PLANES)]
+
+
+class Aggregate(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint32), ("pad", ctypes.c_uint32), ("mass", ctypes.c_double),
+                ("com", ctypes.c_double * 3), ("vel", ctypes.c_double * 3), ("omega", ctypes.c_double * 3),
+                ("inertia", ctypes.c_double * 6)]
 
 
 class LaunchConfig(ctypes.Structure):
@@ -131,6 +145,7 @@ def lib() -> ctypes.CDLL:
         L.tds_batch_read_tool_forces.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_set_graph.argtypes = [vp, ctypes.c_int32]
         L.tds_batch_set_tool_poses.argtypes = [vp, vp, ctypes.c_uint32]
+        L.tds_aggregate_bodies.argtypes = [vp, ctypes.POINTER(Zone), ctypes.c_uint32, ctypes.POINTER(Aggregate)]
         L.tds_get_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
         L.tds_set_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
         L.tds_destroy_scene.argtypes = [vp]
@@ -340,6 +355,29 @@ class Scene:
 
     def set_recording(self, enable: bool = True):
         _check(lib().tds_set_recording(self.h, int(enable)))
+
+    def aggregate_bodies(self, zones) -> list:
+        """Aggregate bodies of the current state. ``zones``: dicts with
+        "planes" ((k, 4) half-spaces n . x <= d) and optionally "scene".
+        Returns per zone a dict of count, mass, com, vel, omega and the 3x3
+        inertia about com."""
+        arr = (Zone * max(1, len(zones)))()
+        for q, z in enumerate(zones):
+            pl = np.asarray(z["planes"], np.float32).reshape(-1, 4)
+            arr[q].scene, arr[q].n_planes = int(z.get("scene", 0)), pl.shape[0]
+            for k in range(min(pl.shape[0], ZONE_MAX_PLANES)):
+                for c in range(4):
+                    arr[q].planes[k][c] = float(pl[k, c])
+        out = (Aggregate * max(1, len(zones)))()
+        _check(lib().tds_aggregate_bodies(self.h, arr, len(zones), out))
+        res = []
+        for q in range(len(zones)):
+            a = out[q]
+            I = np.array(a.inertia[:])
+            res.append({"count": a.count, "mass": a.mass, "com": np.array(a.com[:]), "vel": np.array(a.vel[:]),
+                        "omega": np.array(a.omega[:]),
+                        "inertia": np.array([[I[0], I[3], I[4]], [I[3], I[1], I[5]], [I[4], I[5], I[2]]])})
+        return res
 
     def launch_config(self) -> dict:
         c = LaunchConfig()

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import aggregate as AG
+from paper_2011_00459_gb300.scenes import box_planes
 
 RHO = 2000.0
 
@@ -18,7 +19,7 @@ def mass(r):
 
 
 def big_box():
-    return [{"scene": 0, "planes": AG.box_planes((0.0, 0.0, 0.0), (100.0, 100.0, 100.0))}]
+    return [{"scene": 0, "planes": box_planes((0.0, 0.0, 0.0), (100.0, 100.0, 100.0))}]
 
 
 def test_rigid_motion_is_recovered():
@@ -80,22 +81,22 @@ def test_membership_first_zone_scene_and_faces():
                   [0.75, 0.0, 0.0],  # only in the second
                   [5.0, 5.0, 5.0],   # in none
                   [0.0, 0.0, 0.0]])  # other scene
-    zones = [{"scene": 0, "planes": AG.box_planes((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))},
-             {"scene": 0, "planes": AG.box_planes((0.5, 0.0, 0.0), (0.5, 0.5, 0.5))},
-             {"scene": 1, "planes": AG.box_planes((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))}]
+    zones = [{"scene": 0, "planes": box_planes((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))},
+             {"scene": 0, "planes": box_planes((0.5, 0.0, 0.0), (0.5, 0.5, 0.5))},
+             {"scene": 1, "planes": box_planes((0.0, 0.0, 0.0), (0.5, 0.5, 0.5))}]
     z = AG.zone_of(x, zones, scene_of=[0, 0, 0, 0, 1])
     assert list(z) == [0, 0, 1, -1, 2]
     out = AG.aggregate(x, np.zeros_like(x), np.full(5, 0.05), RHO, zones, scene_of=[0, 0, 0, 0, 1])
     assert [o["count"] for o in out] == [2, 1, 1]
     empty = AG.aggregate(x, np.zeros_like(x), np.full(5, 0.05), RHO,
-                         [{"scene": 0, "planes": AG.box_planes((9, 9, 9), (0.1, 0.1, 0.1))}])[0]
+                         [{"scene": 0, "planes": box_planes((9, 9, 9), (0.1, 0.1, 0.1))}])[0]
     assert empty["count"] == 0 and empty["mass"] == 0.0
 
 
 def test_rotated_box_planes():
     th = 0.6
     R = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
-    zones = [{"scene": 0, "planes": AG.box_planes((1.0, 1.0, 0.0), (0.4, 0.1, 0.2), R)}]
+    zones = [{"scene": 0, "planes": box_planes((1.0, 1.0, 0.0), (0.4, 0.1, 0.2), R)}]
     along = np.array([1.0, 1.0, 0.0]) + 0.35 * R[:, 0]
     across = np.array([1.0, 1.0, 0.0]) + 0.35 * R[:, 1]
     assert list(AG.zone_of(np.stack([along, across]), zones)) == [0, -1]
