@@ -451,6 +451,41 @@ def time_aggregates(g, work, stream, reps: int) -> dict:
             "ms_per_call": e0.elapsed_time(e1) / reps}
 
 
+def time_fields(g, work, stream, reps: int, tds) -> dict:
+    """Coarse-grained fields of the first bed on 0.1 m voxels (voxel kernel and
+    Gaussian with R = l0) and one advection step on that grid: CUDA-event
+    time per call."""
+    import torch
+
+    sc = work[0] if isinstance(work, list) else work
+    lx, ly = sc["footprint"]
+    l0 = 0.1
+    dims = (int(np.ceil(lx / l0)) + 2, int(np.ceil(ly / l0)) + 2, 20)
+    grid = tds.make_grid((-l0, -l0, -0.2), l0, dims, 0)
+    out = {"voxels": int(np.prod(dims)), "l0": l0}
+    for name, kernel, R in (("voxel_kernel_ms", 0, 0.0), ("gaussian_kernel_ms", 1, l0)):
+        g.coarse_grain(grid, kernel, R)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            rho, p, u = g.coarse_grain(grid, kernel, R)
+        e1.record(stream)
+        e1.synchronize()
+        out[name] = e0.elapsed_time(e1) / reps
+    dt = float(l0 / (3.0 * max(float(u.abs().max()), 1e-6)))
+    a = rho.clone()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        a = tds.advect_fluid(grid, u, a, dt, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    out["advect_ms"] = e0.elapsed_time(e1) / reps
+    return out
+
+
 class _Parked:
     """A sim whose steps keep the tools where they are (parked): what the
     autotuner steps while it times launch shapes."""
@@ -575,9 +610,10 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                 torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
                 fms = float(t.item())
             fixed = {"ms": fms, "st": fst, "sweeps": int(first["fixed_iters"])}
-        agg = None
+        agg = fields = None
         if not isinstance(g, SceneGroup):
             agg = time_aggregates(g, work, stream, args.steps)
+            fields = time_fields(g, work, stream, args.steps, tds)
         one = g.scenes[0] if isinstance(g, SceneGroup) else g
         launch_cfg = one.launch_config()
         if tuned:
@@ -611,6 +647,7 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                    "steps": "the same steps as the device-timed region (identical preparation)"}
             g.close()
     launch_cfg["aggregate_bodies"] = agg
+    launch_cfg["fields"] = fields
     return work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg
 
 

@@ -276,6 +276,39 @@ typedef struct {
 } tds_aggregate;
 tds_status tds_aggregate_bodies(tds_scene *s, const tds_zone *zones, uint32_t count, tds_aggregate *out);
 
+/* ---- coarse-grained fields and fluidized-mass advection ---------------------------
+ * Section "Coarse-graining" (Eq. cg_velocity) and the conserved advection of
+ * fluidized mass (Eq. advection) on a voxel grid: voxel (i, j, k) has its
+ * corner at origin + (i, j, k) l0 and index v = (k ny + j) nx + i; vector
+ * fields are interleaved, 3 floats per voxel (x, y, z).
+ * tds_coarse_grain samples, at voxel centres, rho = sum_a m_a zeta(x - x_a),
+ * p = sum_a m_a v_a zeta(x - x_a) and u = p / rho (0 where rho = 0) for the
+ * particles of scene grid->scene after the last step. kernel 0: zeta = 1/l0^3
+ * on the voxel containing the particle centre (FP32 floor((x - o) / l0),
+ * clamped to the grid: mass is preserved exactly); kernel 1: the Gaussian
+ * (sqrt(2 pi) R)^-3 exp(-|x|^2 / 2R^2), truncated beyond 3R. rho (nvox
+ * floats), p and u (3 nvox floats) are device pointers, overwritten;
+ * asynchronous on the scene's stream (FP32 atomic accumulation).
+ * tds_advect_fluid advances rho_f by one first-order upwind finite-volume
+ * step of d rho_f/dt + div(rho_f u) = r_f in a closed grid: the face between
+ * two voxels carries u_f rho_upwind (u_f the mean of their velocity
+ * components normal to the face), boundary faces carry nothing, so the total
+ * mass changes only by dt sum r_f (to rounding). Stable for
+ * max |u| dt / l0 <= 1/3. u, rho_f, source (or NULL) and rho_out (not
+ * aliasing rho_f) are device pointers; stream a cudaStream_t or NULL;
+ * asynchronous. The paper's kinetic and contact stress fields are not
+ * provided. */
+typedef struct {
+  float origin[3];  /* [m] */
+  float l0;         /* voxel size [m] */
+  uint32_t nx, ny, nz;
+  uint32_t scene;   /* scene of a batch whose particles are sampled */
+} tds_grid;
+tds_status tds_coarse_grain(tds_scene *s, const tds_grid *grid, int32_t kernel, float R, float *rho, float *p,
+                            float *u);
+tds_status tds_advect_fluid(const tds_grid *grid, const float *u, const float *rho_f, const float *source,
+                            float dt, float *rho_out, void *stream);
+
 /* ---- launch shapes ------------------------------------------------------------
  * Knobs of the GPU schedule (the paper, a CPU method, has none). Results do
  * not depend on them: every setting gives the same impulses and states bit

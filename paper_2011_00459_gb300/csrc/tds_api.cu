@@ -36,6 +36,9 @@ int tds_pgs_setup(int *threads);
 int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, uint32_t nz, uint8_t *zone_id,
                          double *sums, tds_aggregate *out, cudaStream_t st);
 size_t tds_aggregate_sums_words();
+int tds_launch_coarse_grain(const DevPtrs &d, uint32_t n, const tds_grid &g, int kernel, float R, float *rho,
+                            float *p, float *u, cudaStream_t st);
+bool tds_grid_valid(const tds_grid *g);
 const void *tds_colour_kernel();
 
 namespace {
@@ -1060,6 +1063,21 @@ tds_status tds_aggregate_bodies(tds_scene *s, const tds_zone *zones, uint32_t co
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(out, s->x.agg_out, sizeof(tds_aggregate) * count, cudaMemcpyDeviceToHost, s->st));
   return sync_and_check(s);
+}
+
+tds_status tds_coarse_grain(tds_scene *s, const tds_grid *grid, int32_t kernel, float R, float *rho, float *p,
+                            float *u) {
+  if (!s || !rho || !p || !u) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (!tds_grid_valid(grid)) return fail(TDS_ERR_INVALID_ARG, "invalid grid");
+  if (grid->scene >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "grid scene out of range");
+  if (kernel != 0 && kernel != 1) return fail(TDS_ERR_INVALID_ARG, "kernel must be 0 (voxel) or 1 (Gaussian)");
+  if (kernel == 1 && !(R > 0.0f && R <= 16.0f * grid->l0))
+    return fail(TDS_ERR_INVALID_ARG, "Gaussian smoothing length must be in (0, 16 l0]");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  s->launches += tds_launch_coarse_grain(s->d, s->L.n, *grid, kernel, R, rho, p, u, s->st);
+  CUDA_TRY(cudaGetLastError());
+  return TDS_OK;
 }
 
 tds_status tds_set_mlp_weights(tds_scene *s, const float *params, uint32_t count) {

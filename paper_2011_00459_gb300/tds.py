@@ -32,7 +32,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_warm_start", "tds_batch_workspace_bytes", "tds_create_batch",
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
-            "tds_set_launch_config", "tds_aggregate_bodies"]
+            "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -94,6 +94,34 @@ class Aggregate(ctypes.Structure):
                 ("inertia", ctypes.c_double * 6)]
 
 
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("l0", ctypes.c_float), ("nx", ctypes.c_uint32),
+                ("ny", ctypes.c_uint32), ("nz", ctypes.c_uint32), ("scene", ctypes.c_uint32)]
+
+
+def make_grid(origin, l0: float, dims, scene: int = 0) -> Grid:
+    g = Grid()
+    for a in range(3):
+        g.origin[a] = float(origin[a])
+    g.l0 = float(l0)
+    g.nx, g.ny, g.nz = (int(d) for d in dims)
+    g.scene = int(scene)
+    return g
+
+
+def advect_fluid(grid: Grid, u, rho, dt: float, source=None, out=None, stream=None):
+    """One conserved upwind step of the fluidized-mass density on device
+    tensors (rho: nz x ny x nx, u: nz x ny x nx x 3); returns rho_out."""
+    import torch
+
+    out = torch.empty_like(rho) if out is None else out
+    st = stream if stream is not None else torch.cuda.current_stream()
+    src = ctypes.c_void_p(source.data_ptr()) if source is not None else None
+    _check(lib().tds_advect_fluid(ctypes.byref(grid), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                  src, float(dt), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+    return out
+
+
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pgs_blocks", ctypes.c_int32), ("pgs_sync", ctypes.c_int32),
                 ("colour_blocks", ctypes.c_int32), ("max_pgs_blocks", ctypes.c_int32),
@@ -146,6 +174,8 @@ def lib() -> ctypes.CDLL:
         L.tds_set_graph.argtypes = [vp, ctypes.c_int32]
         L.tds_batch_set_tool_poses.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_aggregate_bodies.argtypes = [vp, ctypes.POINTER(Zone), ctypes.c_uint32, ctypes.POINTER(Aggregate)]
+        L.tds_coarse_grain.argtypes = [vp, ctypes.POINTER(Grid), ctypes.c_int32, ctypes.c_float, vp, vp, vp]
+        L.tds_advect_fluid.argtypes = [ctypes.POINTER(Grid), vp, vp, vp, ctypes.c_float, vp, vp]
         L.tds_get_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
         L.tds_set_launch_config.argtypes = [vp, ctypes.POINTER(LaunchConfig)]
         L.tds_destroy_scene.argtypes = [vp]
@@ -378,6 +408,20 @@ class Scene:
                         "omega": np.array(a.omega[:]),
                         "inertia": np.array([[I[0], I[3], I[4]], [I[3], I[1], I[5]], [I[4], I[5], I[2]]])})
         return res
+
+    def coarse_grain(self, grid: Grid, kernel: int = 0, R: float = 0.0):
+        """Mass density, momentum density and velocity fields of the current
+        state on ``grid`` (torch device tensors: rho (nz, ny, nx), p and u
+        (nz, ny, nx, 3)), computed on the scene's stream."""
+        torch = self._torch
+        shape = (grid.nz, grid.ny, grid.nx)
+        rho = torch.empty(shape, dtype=torch.float32, device="cuda")
+        p = torch.empty(shape + (3,), dtype=torch.float32, device="cuda")
+        u = torch.empty_like(p)
+        _check(lib().tds_coarse_grain(self.h, ctypes.byref(grid), int(kernel), float(R),
+                                      ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(p.data_ptr()),
+                                      ctypes.c_void_p(u.data_ptr())))
+        return rho, p, u
 
     def launch_config(self) -> dict:
         c = LaunchConfig()
