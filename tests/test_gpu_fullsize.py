@@ -1,0 +1,100 @@
+"""Parity at the benchmark's full sizes and launch shapes, and degenerate
+inputs. The oracle steps the same seeded inputs: a jammed 1 000 000-sphere
+block (the large workload's size and radii) with the default launch shape the
+bench times, and 256 jammed beds of log-uniform size (the batched workload's
+count, sizes and radii) stepped as one batch replayed from a CUDA graph.
+Contact sets and colourings bit-exact, impulses within 1e-4, positions within
+1e-6 m; then single and coincident particles."""
+import numpy as np
+import pytest
+
+from paper_2011_00459_gb300 import scenes as S
+from tests.parity_cases import packed_scene, rel_impulse_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tds():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2011_00459_gb300 import build, tds
+
+    build.build()
+    return tds
+
+
+def test_one_million_spheres_one_step(tds, orc):
+    scene = packed_scene(1_000_000, 61, iters=2)
+    st = orc.State(scene)
+    ref = orc.step(scene, st)
+    g = tds.Scene(scene)
+    cfg = g.launch_config()
+    assert cfg["pgs_sync"] == 1 and cfg["pgs_blocks"] == cfg["max_pgs_blocks"]  # the bench's default shape
+    g.step(1)
+    out = g.read_contacts()
+    parts = g.read_particles()
+    stats = g.stats()
+    g.close()
+    assert stats["n_contacts"] == ref["n_contacts"] > 1_500_000
+    assert np.array_equal(out["keys"], ref["keys"])
+    assert np.array_equal(out["colour"].astype(np.int64), ref["colour"].astype(np.int64))
+    assert rel_impulse_error(out["lam"], ref["lam"]) <= 1e-4
+    assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= 1e-6
+
+
+def local_part(out, o, n):
+    keys = out["keys"].astype(np.uint64)
+    a = (keys >> np.uint64(32)).astype(np.int64)
+    sel = (a >= o) & (a < o + n)
+    b = (keys[sel] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    b = np.where((b & 0x80000000) == 0, b - o, b)
+    local = ((a[sel] - o).astype(np.uint64) << np.uint64(32)) | b.astype(np.uint64)
+    order = np.argsort(local, kind="stable")
+    return local[order], out["lam"][sel][order], out["colour"][sel][order]
+
+
+def test_256_beds_one_batch_graph_replay(tds, orc):
+    import torch
+
+    g = S.rng(62)
+    ns = np.exp(g.uniform(np.log(1000), np.log(20000), 256)).astype(int)
+    beds = [packed_scene(int(n), 1000 + q, iters=2, r_lo=0.03, r_hi=0.05) for q, n in enumerate(ns)]
+    b = tds.Batch(beds, stream=torch.cuda.Stream())
+    b.set_graph(True)
+    b.step(1)
+    out = b.read_contacts()
+    xs = [b.read_scene(q)["x"] for q in range(len(beds))]
+    b.close()
+    for q, bed in enumerate(beds):
+        st = orc.State(bed)
+        ref = orc.step(bed, st)
+        keys, lam, col = local_part(out, int(b.offsets[q]), b.sizes[q])
+        assert np.array_equal(keys, ref["keys"]), q
+        assert np.array_equal(col.astype(np.int64), ref["colour"].astype(np.int64)), q
+        assert rel_impulse_error(lam, ref["lam"]) <= 1e-4, q
+        assert np.abs(xs[q].astype(np.float64) - st.x).max() <= 1e-6, q
+
+
+def test_single_particle_and_coincident_particles(tds, orc):
+    base = packed_scene(27, 63, iters=20)
+    one = S.with_particles(base, base["x"][:1] + 0.001, base["r"][:1])
+    x = np.repeat(base["x"][:1], 3, axis=0)  # three particles at one point
+    x = np.concatenate([x, base["x"][1:2]])
+    coincident = S.with_particles(base, x, base["r"][:4])
+    for scene in (one, coincident):
+        st = orc.State(scene)
+        ref = orc.step(scene, st)
+        g = tds.Scene(scene)
+        g.step(1)
+        out = g.read_contacts()
+        parts = g.read_particles()
+        g.close()
+        assert np.array_equal(out["keys"], ref["keys"])
+        assert np.array_equal(out["colour"].astype(np.int64), ref["colour"].astype(np.int64))
+        if len(ref["keys"]):
+            assert rel_impulse_error(out["lam"], ref["lam"]) <= 1e-4
+        assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= 1e-6
+        assert np.isfinite(parts["v"]).all()
