@@ -46,6 +46,8 @@ class OrcParams(ctypes.Structure):
         ("n_tool", ctypes.c_int32), ("tool_boxes", ctypes.POINTER(ctypes.c_float)),
         ("tool_pos", ctypes.c_float * 3), ("tool_quat", ctypes.c_float * 4),
         ("tool_vel", ctypes.c_float * 3), ("tool_angvel", ctypes.c_float * 3),
+        ("restitution", ctypes.c_double), ("impact_speed", ctypes.c_double),
+        ("impact_iters", ctypes.c_int32),
     ]
 
 
@@ -55,6 +57,7 @@ class OrcStats(ctypes.Structure):
         ("n_colours", ctypes.c_int32), ("iterations", ctypes.c_int32),
         ("residual", ctypes.c_double),
         ("tool_force", ctypes.c_double * 3), ("tool_torque", ctypes.c_double * 3),
+        ("impacts", ctypes.c_int32),
     ]
 
 
@@ -121,6 +124,9 @@ class Params:
         p.tol = float(s.get("tol", 0.0))
         p.order = int(s.get("order", 0)); p.warm_start = int(s.get("warm_start", 1))
         p.shuffle_seed = int(s.get("shuffle_seed", 0))
+        p.restitution = float(s.get("restitution", 0.0))
+        p.impact_speed = float(s.get("impact_speed", 0.0))
+        p.impact_iters = int(s.get("impact_iters", 0))
         hf = s.get("hf")
         if hf is not None:
             h = _f32(hf["h"]).reshape(-1)
@@ -217,6 +223,7 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
         "n_contacts": nc, "n_pp": st.n_pp, "n_static": st.n_static,
         "n_colours": st.n_colours, "iterations": st.iterations, "residual": st.residual,
         "tool_force": np.array(st.tool_force[:]), "tool_torque": np.array(st.tool_torque[:]),
+        "impacts": st.impacts,
     }
 
 

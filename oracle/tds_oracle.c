@@ -348,6 +348,7 @@ typedef struct {
   double Dn, Dt, Dr;              /* diagonal of G M^-1 G^T + Sigma per row group */
   double st, sr;                  /* Sigma_bar of the tangent and rolling rows */
   double ln, lt[2], lr[3];        /* impulses */
+  double Gvn;                     /* G_n v_n at the start of the step */
   int colour;
   int persisted;                  /* the key existed in the previous step */
   double W;                       /* impulse scale m_eff |g| h of the learned warm start */
@@ -491,6 +492,7 @@ static void contact_rows(const orc_params *P, const double *r, const masses *M,
   double g = -0.8 * c->delta;
   double dv[3] = {vb[0] - v0[3 * c->a], vb[1] - v0[3 * c->a + 1], vb[2] - v0[3 * c->a + 2]};
   double Gv0 = dot3(c->n, dv);
+  c->Gvn = Gv0;
   c->Sn = 4.0 / (h * h) * ups * eps;
   c->qn = -4.0 / h * ups * g + ups * Gv0;
   c->fc = (P->cohesion > 0.0 && !c->is_tool) ? h * P->cohesion * ORC_PI * rbar * rbar : 0.0;
@@ -817,6 +819,50 @@ static int contact_features(const orc_params *P, int n, const double *x, const d
   return 0;
 }
 
+/* Impact stage (the Newton impact law, section "Contacting rigid
+ * multibodies"), a velocity-level solve before the main one. A contact whose
+ * approach speed at the start of the step, -G_n v_n, exceeds v_imp is an
+ * impact and gets the target G_n v+ = e (-G_n v_n); every other normal row is
+ * held at G_n v+ >= 0; friction and rolling keep their cones; no cohesion.
+ * Rigid rows (no compliance), impulses from zero, impact_iters sweeps in the
+ * main solve's order, acting on the predicted velocities v*. Afterwards the
+ * main solve's q_n = -(4/h) Upsilon g + Upsilon G_n v takes the post-impact
+ * velocities: q_n += Upsilon (G_n v+ - G_n v*). Returns the number of
+ * impacts (0: nothing done). */
+static int impact_stage(const orc_params *P, contact *C, int nc, const int *order, const masses *M,
+                        double *v, double *w) {
+  int nimp = 0;
+  for (int k = 0; k < nc; ++k) nimp += -C[k].Gvn > P->impact_speed;
+  if (P->impact_iters <= 0 || nimp == 0) return 0;
+  contact *I = (contact *)malloc(sizeof(contact) * (nc + 1));
+  double *gv = (double *)malloc(sizeof(double) * (nc + 1));
+  if (!I || !gv) { free(I); free(gv); return -1; }
+  double va[3], wa[3], vb[3], wb[3];
+  for (int k = 0; k < nc; ++k) {
+    I[k] = C[k];
+    contact *c = &I[k];
+    side_velocities(c, v, w, va, wa, vb, wb);
+    double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+    gv[k] = dot3(c->n, dv);
+    c->Dn -= c->Sn;   /* rigid normal row */
+    c->Sn = 0.0;
+    c->qn = -c->Gvn > P->impact_speed ? P->restitution * (-c->Gvn) : 0.0;
+    c->fc = 0.0;      /* no cohesion */
+    c->ln = 0.0; c->lt[0] = c->lt[1] = 0.0; c->lr[0] = c->lr[1] = c->lr[2] = 0.0;
+  }
+  for (int it = 0; it < P->impact_iters; ++it)
+    for (int k = 0; k < nc; ++k) pgs_contact(&I[order[k]], M, v, w);
+  double tau = 2.0 * P->dt, ups = 1.0 / (1.0 + 4.0 * tau / P->dt);
+  for (int k = 0; k < nc; ++k) {
+    contact *c = &C[k];
+    side_velocities(c, v, w, va, wa, vb, wb);
+    double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+    c->qn += ups * (dot3(c->n, dv) - gv[k]);
+  }
+  free(I); free(gv);
+  return nimp;
+}
+
 int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w,
                  const double *r, int32_t n_prev, const uint64_t *prev_keys,
                  const double *prev_lam, int32_t cap, uint64_t *out_keys,
@@ -879,7 +925,8 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < 3; ++k) v[3 * i + k] += h * P->gravity[k];
   /* 3. warm start: previous impulses by key, Lambda_t re-projected onto the
-   *    new tangent plane, all clamped into the new bounds; v += M^-1 G^T lambda_0 */
+   *    new tangent plane, all clamped into the new bounds (v += M^-1 G^T
+   *    lambda_0 follows the impact stage below) */
   for (int k = 0; k < nc; ++k) {
     contact *c = &C[k];
     c->ln = 0.0; c->lt[0] = c->lt[1] = 0.0; c->lr[0] = c->lr[1] = c->lr[2] = 0.0;
@@ -898,14 +945,6 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
   }
   /* learned-warm-start features of every contact at v* with lambda_0 */
   if (contact_features(P, n, x, r, &M, v, w, C, nc)) { rc = -2; goto done; }
-  for (int k = 0; k < nc; ++k) {
-    contact *c = &C[k];
-    if (!c->persisted) continue;
-    double tw0[3] = {c->lt[0] * c->t1[0] + c->lt[1] * c->t2[0],
-                     c->lt[0] * c->t1[1] + c->lt[1] * c->t2[1],
-                     c->lt[0] * c->t1[2] + c->lt[1] * c->t2[2]};
-    apply(c, &M, v, w, c->ln, tw0, c->lr);
-  }
   /* 4. colouring and the sweep order */
   int ncol = colour_contacts(C, nc, n);
   if (ncol < 0) { rc = -2; goto done; }
@@ -932,6 +971,17 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
         }
       }
     }
+  }
+  /* impact stage on v*, then the warm start v += M^-1 G^T lambda_0 */
+  st->impacts = impact_stage(P, C, nc, order, &M, v, w);
+  if (st->impacts < 0) { rc = -2; goto done; }
+  for (int k = 0; k < nc; ++k) {
+    contact *c = &C[k];
+    if (!c->persisted) continue;
+    double tw0[3] = {c->lt[0] * c->t1[0] + c->lt[1] * c->t2[0],
+                     c->lt[0] * c->t1[1] + c->lt[1] * c->t2[1],
+                     c->lt[0] * c->t1[2] + c->lt[1] * c->t2[2]};
+    apply(c, &M, v, w, c->ln, tw0, c->lr);
   }
   /* 5. PGS sweeps */
   int it = 0;

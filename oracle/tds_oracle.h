@@ -59,12 +59,18 @@ typedef struct {
   int32_t n_tool;
   const float *tool_boxes;
   float tool_pos[3], tool_quat[4], tool_vel[3], tool_angvel[3];
+  /* impact stage (section "Contacting rigid multibodies", Newton impact law):
+   * impact_iters == 0 disables it */
+  double restitution;                 /* e */
+  double impact_speed;                /* v_imp [m/s] */
+  int32_t impact_iters;               /* sweeps of the impact solve */
 } orc_params;
 
 typedef struct {
   int32_t n_contacts, n_pp, n_static, n_colours, iterations;
   double residual;
   double tool_force[3], tool_torque[3];
+  int32_t impacts;                    /* contacts treated as impacts this step */
 } orc_stats;
 
 /* Contact keys: ((uint64)a << 32) | b for particles a < b, and
