@@ -114,6 +114,17 @@ typedef struct {
   int32_t warm_start;          /* tds_warm_start */
   uint32_t contacts_per_particle;
   float domain_lo[3], domain_hi[3];
+  /* Impact stage (the Newton impact law of section "Contacting rigid
+   * multibodies"), a velocity-level solve before the main one: a contact whose
+   * approach speed at the start of the step, -G_n v_n, exceeds impact_speed
+   * gets the target G_n v+ = restitution * (-G_n v_n); every other normal row
+   * is held at G_n v+ >= 0; friction and rolling keep their cones; no
+   * cohesion; rigid rows, impulses from zero, impact_iters colour sweeps on the
+   * predicted velocities; the main solve then starts from v+ (its q_n takes the
+   * post-impact normal velocities). impact_iters == 0 disables it. The tool
+   * force reports the main solve's impulses. */
+  float restitution, impact_speed;
+  uint32_t impact_iters;
 } tds_scene_desc;
 
 typedef struct tds_scene tds_scene; /* opaque */
@@ -131,6 +142,7 @@ typedef struct {
      sweeps x particle-pair contacts, sweeps x static contacts, contacts, steps */
   uint64_t sweep_contacts_pp, sweep_contacts_static, sum_contacts, solved_steps;
   uint32_t colour_rounds;      /* rounds of the parallel greedy colouring, last step */
+  uint32_t impacts;            /* contacts treated as impacts, last step */
 } tds_step_stats;
 
 /* Bytes of device workspace a scene with this description needs. */
@@ -153,6 +165,10 @@ tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[
 /* Change the solver settings for the following steps: sweeps (or the cap in
  * residual mode), tol (> 0: residual mode) and the residual check period. */
 tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t residual_every);
+
+/* Change the impact stage (restitution, impact_speed, impact_iters; see
+ * tds_scene_desc) for the following steps. */
+tds_status tds_set_impact(tds_scene *s, float restitution, float impact_speed, uint32_t impact_iters);
 
 /* Change the warm start (tds_warm_start) for the following steps;
  * TDS_WARM_LEARNED needs tds_set_mlp_weights before the next step. */

@@ -30,6 +30,8 @@ void tds_mlp_adam_launch(float *params, float *grad, float *mom, float *vel, uin
 int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
                            uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st);
+cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
+                              int blocks, cudaStream_t st);
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 int tds_pgs_setup(int *threads);
@@ -121,12 +123,13 @@ struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
 struct GraphKey {
   int use_prev = -1, warm = -1, recording = -1, timing = -1;
   int pgs_blocks = -1, pgs_sync = -1, colour_blocks = -1;
-  uint32_t max_iters = 0, every = 0;
-  float tol = -1.f;
+  uint32_t max_iters = 0, every = 0, impact_iters = 0;
+  float tol = -1.f, restitution = -1.f, impact_speed = -1.f;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
            pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && colour_blocks == o.colour_blocks &&
-           max_iters == o.max_iters && every == o.every && tol == o.tol;
+           max_iters == o.max_iters && every == o.every && tol == o.tol && impact_iters == o.impact_iters &&
+           restitution == o.restitution && impact_speed == o.impact_speed;
   }
 };
 
@@ -195,6 +198,9 @@ tds_status validate(const tds_scene_desc *d) {
   if (d->max_iters == 0) return fail(TDS_ERR_INVALID_ARG, "max_iters must be >= 1");
   if (d->warm_start != TDS_WARM_COLD && d->warm_start != TDS_WARM_PREV && d->warm_start != TDS_WARM_LEARNED)
     return fail(TDS_ERR_INVALID_ARG, "warm_start must be TDS_WARM_COLD, TDS_WARM_PREV or TDS_WARM_LEARNED");
+  if (!(d->restitution >= 0.f && d->restitution <= 1.f) || !(d->impact_speed >= 0.f) ||
+      !std::isfinite(d->impact_speed))
+    return fail(TDS_ERR_INVALID_ARG, "restitution must be in [0, 1] and impact_speed >= 0");
   for (uint32_t i = 0; i < d->n; ++i)
     if (!(d->radius[i] > 0.f) || !std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) ||
         !std::isfinite(d->z[i]))
@@ -215,10 +221,11 @@ tds_status validate_batch(const tds_scene_desc *descs, uint32_t count) {
         a.gravity[2] != b.gravity[2] || a.density != b.density || a.young != b.young ||
         a.poisson != b.poisson || a.cohesion != b.cohesion || a.max_iters != b.max_iters ||
         a.tol != b.tol || a.residual_every != b.residual_every || a.warm_start != b.warm_start ||
-        a.contacts_per_particle != b.contacts_per_particle)
+        a.contacts_per_particle != b.contacts_per_particle || a.restitution != b.restitution ||
+        a.impact_speed != b.impact_speed || a.impact_iters != b.impact_iters)
       return fail(TDS_ERR_INVALID_ARG,
                   "scenes of a batch must share dt, gravity, density, young, poisson, cohesion, the "
-                  "solver settings, warm_start and contacts_per_particle");
+                  "solver settings, warm_start, contacts_per_particle and the impact stage");
   }
   if (total >= 0x7FFFFFFFull) return fail(TDS_ERR_INVALID_ARG, "too many particles in the batch");
   return TDS_OK;
@@ -366,6 +373,7 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.p_rm = c.take<float2>(pc);
   d.p_sv = c.take<float4>(pc); d.p_sw = c.take<float4>(pc);
   d.p_la = c.take<float4>(pc); d.p_lb = c.take<float2>(pc);
+  d.p_il = c.take<float4>(pc); d.p_il2 = c.take<float4>(pc);
   for (int b = 0; b < 2; ++b) {
     d.prev_first[b] = c.take<uint32_t>(n);
     d.prev_cnt[b] = c.take<uint32_t>(n);
@@ -674,6 +682,10 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool c
     launches += 1;
   }
   launches += tds_launch_bucketing(d, s->L.cap, s->st);
+  if (D.impact_iters > 0) {
+    CUDA_TRY(tds_launch_impact(d, s->k, D.restitution, D.impact_speed, D.impact_iters, s->pgs_blocks, s->st));
+    launches += 1;
+  }
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[3], s->st, evf));
   CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned, s->pgs_blocks,
                           s->pgs_sync, s->st));
@@ -701,6 +713,9 @@ GraphKey graph_key(const tds_scene *s) {
   g.pgs_blocks = s->pgs_blocks;
   g.pgs_sync = s->pgs_sync;
   g.colour_blocks = s->colour_blocks;
+  g.impact_iters = s->desc.impact_iters;
+  g.restitution = s->desc.restitution;
+  g.impact_speed = s->desc.impact_speed;
   return g;
 }
 
@@ -844,6 +859,16 @@ tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t 
   return TDS_OK;
 }
 
+tds_status tds_set_impact(tds_scene *s, float restitution, float impact_speed, uint32_t impact_iters) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (!(restitution >= 0.f && restitution <= 1.f) || !(impact_speed >= 0.f) || !std::isfinite(impact_speed))
+    return fail(TDS_ERR_INVALID_ARG, "restitution must be in [0, 1] and impact_speed >= 0");
+  s->desc.restitution = restitution;
+  s->desc.impact_speed = impact_speed;
+  s->desc.impact_iters = impact_iters;
+  return TDS_OK;
+}
+
 tds_status tds_set_warm_start(tds_scene *s, int32_t mode) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
   if (mode != TDS_WARM_COLD && mode != TDS_WARM_PREV && mode != TDS_WARM_LEARNED)
@@ -983,6 +1008,7 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   out->n_pp = ctr[CTR_NC] - nst;
   out->n_colours = ctr[CTR_NCOL];
   out->colour_rounds = ctr[CTR_ROUNDS];
+  out->impacts = s->desc.impact_iters ? ctr[CTR_IMPACTS] : 0;
   out->iterations = ctr[CTR_ITERS];
   out->residual = fs[FS_RESID];
   out->steps = s->steps;

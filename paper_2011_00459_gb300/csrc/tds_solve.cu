@@ -629,6 +629,77 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   }
 }
 
+// Impact stage (the Newton impact law): a rigid velocity-level solve on the
+// predicted velocities v* before the main solve. Pass 0 classifies every
+// contact by its approach speed at the start of the step, -G_n v_n (G_n v* for
+// a particle pair; G_n v* + h n.g against a static surface, which does not
+// fall), sets the normal target e * approach for impacts and 0 otherwise, and
+// zeroes the stage's impulses; with no impact the kernel stops there. Then
+// `iters` colour sweeps of the main solve's update on rows with no compliance
+// (Sigma_n = 0), that target as q_n and no cohesion; finally every contact's
+// q_n takes the post-impact normal velocity: q_n += Upsilon (G_n v+ - G_n v*).
+struct ImpactArgs {
+  float e, vimp, h, g[3], ups, sig_t, sig_r;
+  uint32_t iters;
+};
+
+__global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
+  __shared__ uint32_t s_count;
+  const uint32_t ncol = min(d.ctr[CTR_NCOL], (uint32_t)TDS_MAX_COLOURS);
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  uint32_t gen = 0;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  uint32_t mine = 0;
+  for (uint32_t col = 0; col < ncol; ++col)
+    for (int part = 0; part < 2; ++part)
+      for (uint32_t p = d.bstart[2 * col + part] + tid; p < d.bend[2 * col + part]; p += stride) {
+        const Row r = load_row(d, p);
+        Side A, B;
+        load_pair(d, r, A, B);
+        const float gv = dot(r.n, B.v - A.v);
+        const float gvn = r.dyn ? gv : gv + a.h * (r.n.x * a.g[0] + r.n.y * a.g[1] + r.n.z * a.g[2]);
+        const bool hit = -gvn > a.vimp;
+        mine += hit;
+        d.p_il[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        d.p_il2[p] = make_float4(0.f, 0.f, gv, hit ? a.e * -gvn : 0.f);
+      }
+  if (mine) atomicAdd(&s_count, mine);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_count) atomicAdd(d.ctr + CTR_IMPACTS, s_count);
+  if (!grid_barrier(d.bar, d.err, gen)) return;
+  if (*(volatile uint32_t *)(d.ctr + CTR_IMPACTS) == 0) return;  // the same value in every CTA
+  for (uint32_t it = 0; it < a.iters; ++it)
+    for (uint32_t col = 0; col < ncol; ++col) {
+      for (int part = 0; part < 2; ++part)
+        for (uint32_t p = d.bstart[2 * col + part] + tid; p < d.bend[2 * col + part]; p += stride) {
+          Row r = load_row(d, p);
+          const float4 t = d.p_il2[p];
+          r.Sn = 0.f;
+          r.fc = 0.f;
+          r.qn = t.w;
+          float4 L0 = d.p_il[p];
+          float2 L1 = make_float2(t.x, t.y);
+          Side A, B;
+          load_pair(d, r, A, B);
+          pgs_update(r, A, B, L0, L1, a.sig_t, a.sig_r);
+          store_side(d, r.ab.x, A);
+          if (r.dyn) store_side(d, r.ab.y, B);
+          d.p_il[p] = L0;
+          d.p_il2[p] = make_float4(L1.x, L1.y, t.z, t.w);
+        }
+      if (!grid_barrier(d.bar, d.err, gen)) return;
+    }
+  for (uint32_t col = 0; col < ncol; ++col)
+    for (int part = 0; part < 2; ++part)
+      for (uint32_t p = d.bstart[2 * col + part] + tid; p < d.bend[2 * col + part]; p += stride) {
+        const Row r = load_row(d, p);
+        Side A, B;
+        load_pair(d, r, A, B);
+        d.p_rq[p].y = r.qn + a.ups * (dot(r.n, B.v - A.v) - d.p_il2[p].z);
+      }
+}
+
 // Colour order -> owner order warm-start memory: (key's other side,
 // impulses with the tangent in world coordinates); per particle id the range
 // of its owned contacts.
@@ -768,6 +839,16 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
   void *args[] = {&dd, &a};
   return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(kPgsThreads), args,
                                      kPgsSmem, st);
+}
+
+cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
+                              int blocks, cudaStream_t st) {
+  ImpactArgs a{e, vimp, k.dt, {k.g[0], k.g[1], k.g[2]}, k.ups, k.sig_t, k.sig_r, iters};
+  cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
+  cudaMemsetAsync(d.ctr + CTR_IMPACTS, 0, sizeof(uint32_t), st);
+  DevPtrs dd = d;
+  void *args[] = {&dd, &a};
+  return cudaLaunchCooperativeKernel((const void *)k_impact, dim3(blocks), dim3(512), args, 0, st);
 }
 
 // Opt the solver into its shared-memory stages; returns the co-resident

@@ -415,8 +415,39 @@ def batched(seed: int = 0, scenes: int = 256, n_lo: int = 1000, n_hi: int = 2000
                         1000 * seed + q + 1) for q in range(scenes)]
 
 
+def bent_blade(width: float, height: float, thickness: float, angle_deg: float) -> np.ndarray:
+    """A blade of two plates stacked vertically, each half the height: the
+    lower one upright, the upper one turned by angle_deg about the blade's
+    top edge of the lower plate, towards the pushing direction (+x)."""
+    h2 = 0.5 * height
+    lower = box((0.0, 0.0, -0.5 * h2), (0.5 * thickness, 0.5 * width, 0.5 * h2))
+    a = math.radians(angle_deg)
+    # centre of the upper plate: from the joint (0, 0, 0) along its own up axis
+    up = (math.sin(a), 0.0, math.cos(a))
+    upper = box((0.5 * h2 * up[0], 0.0, 0.5 * h2 * up[2]), (0.5 * thickness, 0.5 * width, 0.5 * h2),
+                quat_axis_angle((0.0, 1.0, 0.0), a))
+    return np.stack([lower, upper]).astype(np.float32)
+
+
+def microscale(seed: int = 0, n: int = 50000) -> dict:
+    """The paper's microscale reference configuration: 50 000 spheres of
+    45-55 mm diameter and 2200 kg/m^3 (E 1 GPa, nu 0.15, restitution 0),
+    sand-1 particle parameters (mu 0.3, mu_r 0.1, no cohesion), h = 1 ms and
+    500 PGS sweeps, bulldozed by a 1.6 m wide, 0.37 m tall blade of two plates
+    at 55 degrees cutting 0.05 m deep at 0.5 m/s over 5 m. The impact stage
+    treats approaches faster than 0.5 m/s as impacts (20 sweeps)."""
+    p = base_params(density=2200.0, young=1e9, poisson=0.15, mu_t=0.3, mu_r=0.1, cohesion=0.0,
+                    dt=1e-3, iters=500, restitution=0.0, impact_speed=0.5, impact_iters=20,
+                    hf=flat_heightfield(150, 50, -0.3, -0.3, 0.05),
+                    walls=bed_walls(7.0, 2.0, 3.0), tool_boxes=bent_blade(1.6, 0.37, 0.02, 55.0))
+    s = _spawned(p, n, 7.0, 2.0, 0.0225, 0.0275, seed, 0.0)
+    s.update(name="microscale", steps=10000, footprint=(7.0, 2.0), blade_speed=0.5, blade_depth=0.05,
+             blade_height=0.37, tool_kind="blade", settle_steps=600)
+    return s
+
+
 WORKLOADS = {"small": small, "bulldozing": bulldozing, "excavation": excavation,
-             "large": large}
+             "large": large, "microscale": microscale}
 
 
 def tool_path(scene: dict, surface: float, seed: int = 0):

@@ -32,7 +32,8 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_warm_start", "tds_batch_workspace_bytes", "tds_create_batch",
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
-            "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid"]
+            "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid",
+            "tds_set_impact"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -64,6 +65,7 @@ class SceneDesc(ctypes.Structure):
         ("max_iters", ctypes.c_uint32), ("tol", _f), ("residual_every", ctypes.c_uint32),
         ("warm_start", ctypes.c_int32), ("contacts_per_particle", ctypes.c_uint32),
         ("domain_lo", _f * 3), ("domain_hi", _f * 3),
+        ("restitution", _f), ("impact_speed", _f), ("impact_iters", ctypes.c_uint32),
     ]
 
 
@@ -75,7 +77,7 @@ class StepStats(ctypes.Structure):
                 ("timed_steps", ctypes.c_uint32), ("phase_ms", ctypes.c_float * 5),
                 ("sweep_contacts_pp", ctypes.c_uint64), ("sweep_contacts_static", ctypes.c_uint64),
                 ("sum_contacts", ctypes.c_uint64), ("solved_steps", ctypes.c_uint64),
-                ("colour_rounds", ctypes.c_uint32)]
+                ("colour_rounds", ctypes.c_uint32), ("impacts", ctypes.c_uint32)]
 
 PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
 
@@ -158,6 +160,7 @@ def lib() -> ctypes.CDLL:
         L.tds_set_mlp_weights.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_set_recording.argtypes = [vp, ctypes.c_int32]
         L.tds_set_warm_start.argtypes = [vp, ctypes.c_int32]
+        L.tds_set_impact.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
         L.tds_read_training_samples.argtypes = [vp, vp, vp, vp, ctypes.c_uint32,
                                                 ctypes.POINTER(ctypes.c_uint32)]
         L.tds_mlp_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -250,6 +253,9 @@ def _make_desc(s: dict, contacts_per_particle: int, domain):
     d.residual_every = int(s.get("residual_every", 10))
     d.warm_start = int(s.get("warm_start", 1))
     d.contacts_per_particle = int(contacts_per_particle)
+    d.restitution = float(s.get("restitution", 0.0))
+    d.impact_speed = float(s.get("impact_speed", 0.0))
+    d.impact_iters = int(s.get("impact_iters", 0))
     if domain is not None:
         for i in range(3):
             d.domain_lo[i], d.domain_hi[i] = domain[0][i], domain[1][i]
@@ -379,6 +385,10 @@ class Scene:
     def set_mlp_weights(self, params: np.ndarray):
         p = np.ascontiguousarray(np.asarray(params, np.float32).reshape(-1))
         _check(lib().tds_set_mlp_weights(self.h, ctypes.c_void_p(p.ctypes.data), p.size))
+
+    def set_impact(self, restitution: float, impact_speed: float, iters: int):
+        """Impact stage settings (iters 0 disables it)."""
+        _check(lib().tds_set_impact(self.h, float(restitution), float(impact_speed), int(iters)))
 
     def set_warm_start(self, mode: int):
         _check(lib().tds_set_warm_start(self.h, int(mode)))
