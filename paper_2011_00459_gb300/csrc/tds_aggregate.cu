@@ -3,9 +3,8 @@
 // centre of mass, velocity, inertia tensor about the centre of mass and the
 // angular velocity I^+ L of the particles it contains. Two passes, as in the
 // definition: (1) membership, M, sum m x, sum m v; (2) the second moments and
-// angular momentum about the centre of mass. FP64 accumulation; each thread
-// walks a contiguous run of slots (spatially sorted, so zones change rarely)
-// and flushes its running sums into shared memory when the zone changes.
+// angular momentum about the centre of mass. FP64 accumulation, reduced warp
+// by warp (see WarpSums).
 #include "tds_internal.cuh"
 
 namespace {
@@ -31,19 +30,61 @@ __device__ __forceinline__ int zone_of(const tds_zone *zones, uint32_t nz, uint3
   return -1;
 }
 
+// Warp-synchronous accumulation of K sums per zone. Each warp walks its own
+// contiguous stretch of slots, 32 consecutive particles per iteration
+// (coalesced). When every particle of the iteration that lies in a zone lies
+// in the same zone (the usual case: slot order is spatial) the warp reduces
+// the K values with shuffles and lane c keeps component c of the running sum
+// of the warp's current zone, flushed into shared memory when the zone
+// changes; iterations that straddle zones add lane by lane.
 template <int K>
-__device__ __forceinline__ void flush(double *sh, int z, const double *acc) {
-  if (z < 0) return;
+struct WarpSums {
+  int cur = -1;
+  double acc = 0.0;  // lane c < K: component c for zone cur
+  __device__ void flush(double *sh, int lane) {
+    if (cur >= 0 && lane < K && acc != 0.0) atomicAdd(sh + cur * K + lane, acc);
+    acc = 0.0;
+  }
+  __device__ void add(double *sh, int lane, int z, const double (&val)[K]) {
+    const unsigned full = 0xffffffffu;
+    const int zsel = __reduce_max_sync(full, z);
+    if (zsel < 0) return;
+    const bool uniform = __all_sync(full, z < 0 || z == zsel);
+    if (!uniform) {
+      if (z >= 0)
 #pragma unroll
-  for (int j = 0; j < K; ++j)
-    if (acc[j] != 0.0) atomicAdd(sh + z * K + j, acc[j]);
-}
+        for (int c = 0; c < K; ++c)
+          if (val[c] != 0.0) atomicAdd(sh + z * K + c, val[c]);
+      return;
+    }
+    if (zsel != cur) {
+      flush(sh, lane);
+      cur = zsel;
+    }
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+      double t = val[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+      if (lane == c) acc += t;
+    }
+  }
+};
 
 template <int K>
 __device__ __forceinline__ void block_to_global(double *sh, double *sums, uint32_t nz) {
   __syncthreads();
   for (uint32_t q = threadIdx.x; q < nz * K; q += blockDim.x)
     if (sh[q] != 0.0) atomicAdd(sums + q, sh[q]);
+}
+
+// The stretch [lo, hi) of slots of this warp (a multiple of 32 long).
+__device__ __forceinline__ void warp_stretch(uint32_t n, uint32_t &lo, uint32_t &hi) {
+  const uint32_t nw = gridDim.x * (blockDim.x >> 5), w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  uint32_t per = (n + nw - 1) / nw;
+  per = (per + 31u) & ~31u;
+  lo = min(n, w * per);
+  hi = min(n, lo + per);
 }
 
 __global__ void __launch_bounds__(kAggThreads) k_agg_first(DevPtrs d, uint32_t n, const tds_zone *zones,
@@ -54,30 +95,30 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_first(DevPtrs d, uint32_t n
     reinterpret_cast<uint32_t *>(sz)[q] = reinterpret_cast<const uint32_t *>(zones)[q];
   for (uint32_t q = threadIdx.x; q < nz * kFirst; q += blockDim.x) sh[q] = 0.0;
   __syncthreads();
-  const uint32_t nt = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t per = (n + nt - 1) / nt;
-  const uint32_t i0 = min(n, t * per), i1 = min(n, i0 + per);
-  double acc[kFirst] = {};
-  int cur = -1;
-  for (uint32_t i = i0; i < i1; ++i) {
-    const float4 p = d.pos[i];
-    const int z = zone_of(sz, nz, d.sid[i], p);
-    zone_id[i] = z < 0 ? 0xFF : (uint8_t)z;
-    if (z < 0) continue;
-    if (z != cur) {
-      flush<kFirst>(sh, cur, acc);
-#pragma unroll
-      for (int j = 0; j < kFirst; ++j) acc[j] = 0.0;
-      cur = z;
+  const int lane = threadIdx.x & 31;
+  uint32_t lo, hi;
+  warp_stretch(n, lo, hi);
+  WarpSums<kFirst> ws;
+  for (uint32_t base = lo; base < hi; base += 32) {
+    const uint32_t i = base + lane;
+    int z = -1;
+    double val[kFirst] = {};
+    if (i < hi) {
+      const float4 p = d.pos[i];
+      z = zone_of(sz, nz, d.sid[i], p);
+      zone_id[i] = z < 0 ? 0xFF : (uint8_t)z;
+      if (z >= 0) {
+        const float4 v = d.pv[2 * (size_t)i];
+        const double m = 1.0 / (double)v.w;
+        val[0] = m;
+        val[1] = m * p.x; val[2] = m * p.y; val[3] = m * p.z;
+        val[4] = m * v.x; val[5] = m * v.y; val[6] = m * v.z;
+        val[7] = 1.0;
+      }
     }
-    const float4 v = d.pv[2 * (size_t)i];
-    const double m = 1.0 / (double)v.w;
-    acc[0] += m;
-    acc[1] += m * p.x; acc[2] += m * p.y; acc[3] += m * p.z;
-    acc[4] += m * v.x; acc[5] += m * v.y; acc[6] += m * v.z;
-    acc[7] += 1.0;
+    ws.add(sh, lane, z, val);
   }
-  flush<kFirst>(sh, cur, acc);
+  ws.flush(sh, lane);
   block_to_global<kFirst>(sh, sums, nz);
 }
 
@@ -92,32 +133,29 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_second(DevPtrs d, uint32_t 
   }
   for (uint32_t q = threadIdx.x; q < nz * kSecond; q += blockDim.x) sh[q] = 0.0;
   __syncthreads();
-  const uint32_t nt = gridDim.x * blockDim.x, t = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t per = (n + nt - 1) / nt;
-  const uint32_t i0 = min(n, t * per), i1 = min(n, i0 + per);
-  double acc[kSecond] = {};
-  int cur = -1;
-  for (uint32_t i = i0; i < i1; ++i) {
-    const uint8_t zb = zone_id[i];
-    if (zb == 0xFF) continue;
-    const int z = zb;
-    if (z != cur) {
-      flush<kSecond>(sh, cur, acc);
-#pragma unroll
-      for (int j = 0; j < kSecond; ++j) acc[j] = 0.0;
-      cur = z;
+  const int lane = threadIdx.x & 31;
+  uint32_t lo, hi;
+  warp_stretch(n, lo, hi);
+  WarpSums<kSecond> ws;
+  for (uint32_t base = lo; base < hi; base += 32) {
+    const uint32_t i = base + lane;
+    int z = -1;
+    double val[kSecond] = {};
+    if (i < hi && zone_id[i] != 0xFF) {
+      z = zone_id[i];
+      const float4 p = d.pos[i];
+      const float4 v = d.pv[2 * (size_t)i];
+      const double m = 1.0 / (double)v.w;
+      const double dx = (double)p.x - com[z][0], dy = (double)p.y - com[z][1], dz = (double)p.z - com[z][2];
+      val[0] = m * dx * dx; val[1] = m * dy * dy; val[2] = m * dz * dz;
+      val[3] = m * dx * dy; val[4] = m * dx * dz; val[5] = m * dy * dz;
+      val[6] = m * (dy * v.z - dz * v.y);
+      val[7] = m * (dz * v.x - dx * v.z);
+      val[8] = m * (dx * v.y - dy * v.x);
     }
-    const float4 p = d.pos[i];
-    const float4 v = d.pv[2 * (size_t)i];
-    const double m = 1.0 / (double)v.w;
-    const double dx = (double)p.x - com[z][0], dy = (double)p.y - com[z][1], dz = (double)p.z - com[z][2];
-    acc[0] += m * dx * dx; acc[1] += m * dy * dy; acc[2] += m * dz * dz;
-    acc[3] += m * dx * dy; acc[4] += m * dx * dz; acc[5] += m * dy * dz;
-    acc[6] += m * (dy * v.z - dz * v.y);
-    acc[7] += m * (dz * v.x - dx * v.z);
-    acc[8] += m * (dx * v.y - dy * v.x);
+    ws.add(sh, lane, z, val);
   }
-  flush<kSecond>(sh, cur, acc);
+  ws.flush(sh, lane);
   block_to_global<kSecond>(sh, sums, nz);
 }
 
@@ -198,7 +236,9 @@ int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, ui
   cudaMemsetAsync(sums, 0, sizeof(double) * TDS_MAX_ZONES * (kFirst + kSecond), st);
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  uint32_t blocks = (n + 8u * kAggThreads - 1) / (8u * kAggThreads);  // ~8 slots per thread
+  // 8 blocks per SM (the warps walk stretches of ~n / (64 SMs) slots), fewer
+  // for small n so that every warp has at least 128 slots
+  uint32_t blocks = (n + 128u * (kAggThreads / 32) - 1) / (128u * (kAggThreads / 32));
   if (blocks < 1) blocks = 1;
   if (blocks > (uint32_t)(8 * sms)) blocks = 8 * sms;
   k_agg_first<<<blocks, kAggThreads, 0, st>>>(d, n, zones, nz, zone_id, first);
