@@ -51,6 +51,28 @@ BYTES_PP = 204.0      # per particle-pair contact per sweep
 BYTES_STATIC = 160.0  # per static contact per sweep
 
 
+def reduce_max(value: float, world: int, device: str = "cuda") -> float:
+    """The largest value over the ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device: str = "cuda") -> float:
+    """The sum over the ranks (particles of all replicas)."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t)
+    return float(t.item())
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,15 +597,8 @@ def run_tds(args, rank: int, world: int, local_rank: int):
         clk = clocks.stop()
         st = g.stats()
         launches = st["kernel_launches"] - launches0
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-            tot = torch.tensor([float(n)], device="cuda")
-            torch.distributed.all_reduce(tot)
-            n_all = float(tot.item())
-        else:
-            n_all = float(n)
+        ms = reduce_max(ms, world)
+        n_all = reduce_sum(n, world)
         g.set_timing(False)
         # ---- fixed sweeps (the roofline region), same bed continuing its dig ----
         fixed = None
@@ -605,10 +620,7 @@ def run_tds(args, rank: int, world: int, local_rank: int):
             fms = f0.elapsed_time(f1)
             fst = g.stats()
             g.set_timing(False)
-            if world > 1:
-                t = torch.tensor([fms], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                fms = float(t.item())
+            fms = reduce_max(fms, world)
             fixed = {"ms": fms, "st": fst, "sweeps": int(first["fixed_iters"])}
         agg = fields = None
         if not isinstance(g, SceneGroup):
@@ -636,10 +648,7 @@ def run_tds(args, rank: int, world: int, local_rank: int):
                 sim.read_back(xs)
             t_e2e = time.perf_counter() - t0
             est = g.stats()
-            if world > 1:
-                t = torch.tensor([t_e2e], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                t_e2e = float(t.item())
+            t_e2e = reduce_max(t_e2e, world)
             e2e = {"value": n_all * args.steps / t_e2e, "unit": UNIT,
                    "h2d_bytes_per_step": sim.h2d_bytes(), "d2h_bytes_per_step": sim.d2h_bytes(),
                    "mean_sweeps": (est["sweep_contacts_pp"] + est["sweep_contacts_static"])
