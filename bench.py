@@ -3,7 +3,7 @@
 Default workload: the 1 000 000-sphere excavation bed (r ~ U[0.02, 0.03] m,
 8 x 8 m, 1024^2 heightfield, 12-box bucket on a seeded spline dig, c_p 5 kPa,
 previous-step warm start), each step's PGS solved to the 1e-4 residual (cap
-2000 sweeps, checked every 5). The bed is spawned on a jittered lattice and
+2000 sweeps, adaptive check schedule). The bed is spawned on a jittered lattice and
 settled untimed on the GPU; the bucket then approaches its deepest cut
 untimed, and the timed steps dig. ``--workload batched`` times 256
 independent beds in one batch (graph replay); ``--unbatched`` the same beds
@@ -208,7 +208,7 @@ def _apply_args(scene: dict, args) -> dict:
     if args.tol > 0:
         scene["tol"] = args.tol
         scene["iters"] = args.max_iters
-        scene["residual_every"] = 5
+        scene["residual_every"] = 0  # adaptive check schedule (same stopping criterion)
     if args.cold:
         scene["warm_start"] = 0
     return scene
@@ -678,6 +678,8 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
     r_lo, r_hi = float(scene["r"].min()), float(scene["r"].max())
     x, r = S.lattice_spawn(n, 0.5, 0.5, r_lo, r_hi, 0.0, seed)
     p = dict(scene)
+    if p.get("tol", 0) > 0 and not p.get("residual_every"):
+        p["residual_every"] = 5  # the oracle checks at a fixed period
     p["walls"] = S.bed_walls(0.5, 0.5, 6.0)
     p["hf"] = S.flat_heightfield(12, 12, -0.05, -0.05, 0.05)
     p["tool_boxes"] = np.zeros((0, 10), np.float32)

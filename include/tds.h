@@ -82,7 +82,10 @@ typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1, TDS_WARM_LEARNED = 2 } tds_
  * Solver (SPOOK, tau_n = 2 dt; PGS): time step dt, gravity, sweeps per step
  *   (max_iters). tol > 0 switches to residual mode: stop when the
  *   diagonally scaled natural-map residual is <= tol, checked every
- *   residual_every sweeps, at most max_iters sweeps.
+ *   residual_every sweeps, at most max_iters sweeps. residual_every = 0 checks
+ *   adaptively: first after 5 sweeps, then where the residual's geometric
+ *   decay between the last two checks predicts the tolerance (2 to 64 sweeps
+ *   on); the criterion is the same, only the check schedule differs.
  * Capacity: contacts_per_particle (0 = 10) bounds the contact count by
  *   contacts_per_particle * n; exceeding it is TDS_ERR_CAPACITY.
  * Broadphase domain: particles are binned in a uniform grid over the box
@@ -163,7 +166,8 @@ tds_status tds_set_tool_pose(tds_scene *s, const float pos[3], const float quat[
                              const float linvel[3], const float angvel[3]);
 
 /* Change the solver settings for the following steps: sweeps (or the cap in
- * residual mode), tol (> 0: residual mode) and the residual check period. */
+ * residual mode), tol (> 0: residual mode) and the residual check period
+ * (0: adaptive, see tds_scene_desc). */
 tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t residual_every);
 
 /* Change the impact stage (restitution, impact_speed, impact_iters; see

@@ -855,7 +855,7 @@ tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t 
   if (max_iters == 0 || !(tol >= 0.f)) return fail(TDS_ERR_INVALID_ARG, "max_iters >= 1 and tol >= 0 required");
   s->desc.max_iters = max_iters;
   s->desc.tol = tol;
-  s->desc.residual_every = residual_every ? residual_every : 1;
+  s->desc.residual_every = residual_every;  // 0: adaptive checks
   return TDS_OK;
 }
 

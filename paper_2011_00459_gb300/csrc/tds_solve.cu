@@ -198,6 +198,7 @@ constexpr int kPgsThreads = 512;
 constexpr int kPerThread = 3;                        // contacts per thread per wave
 constexpr int kWave = kPgsThreads * kPerThread;      // contacts per wave
 constexpr int kStages = 2;                           // waves in flight
+constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
 //              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
 constexpr size_t kRowBytes = 72;
@@ -509,6 +510,12 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   bool ok = true;
   uint32_t it = 0;
   float resid = -1.f;
+  // residual checks: every `every` sweeps, or (every == 0) where the decay
+  // seen so far says the tolerance will be met (see below)
+  __shared__ uint32_t s_next;
+  uint32_t next_check = a.every ? a.every : kFirstCheck;
+  float prev_res = -1.f;
+  uint32_t prev_it = 0;
   while (ok && it < a.max_iters) {
     for (uint32_t col = 0; col < ncol; ++col) {
       const uint32_t phase = it * ncol + col + 1u;
@@ -580,7 +587,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
     }
     if (!ok) break;
     ++it;
-    if (it == a.max_iters || (a.tol > 0.f && it % a.every == 0)) {
+    if (it == a.max_iters || (a.tol > 0.f && it == next_check)) {
       // the residual reads every contact: all colours of this sweep first
       if (a.sync && !grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
       double num = 0.0, den = 0.0;
@@ -607,8 +614,25 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         }
         resid = (float)(sqrt(tn) / fmax(sqrt(td), 1e-12));
         s_flag = a.tol > 0.f && resid <= a.tol;
+        // next check: a fixed period, or the sweep where the geometric decay
+        // measured between the last two checks reaches the tolerance (at
+        // least 2 and at most 64 sweeps on); every CTA computes the same
+        // value from the same residuals
+        uint32_t gap = a.every;
+        if (a.every == 0) {
+          gap = kFirstCheck;
+          if (prev_res > 0.f && resid < prev_res && resid > a.tol) {
+            const double rate = log((double)resid / (double)prev_res) / (double)(it - prev_it);
+            const double need = ceil(log((double)a.tol / (double)resid) / rate);
+            gap = (uint32_t)fmin(64.0, fmax(2.0, need));
+          }
+          prev_res = resid;
+          prev_it = it;
+        }
+        s_next = it + gap;
       }
       __syncthreads();
+      next_check = s_next;
       if (s_flag) break;
     }
   }
@@ -832,7 +856,7 @@ int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
 
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
                            uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st) {
-  SolveArgs a{max_iters, every ? every : 1u, tol, k.sig_t, k.sig_r, apply_warm, sync};
+  SolveArgs a{max_iters, every, tol, k.sig_t, k.sig_r, apply_warm, sync};
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
   if (sync) cudaMemsetAsync(d.prog, 0, sizeof(uint32_t) * kProgStride * (size_t)blocks, st);
   DevPtrs dd = d;

@@ -127,3 +127,31 @@ def test_steps_are_deterministic(tds):
         assert np.array_equal(pa[k], pb[k])
     assert np.array_equal(ca["lam"], cb["lam"])
     assert np.array_equal(fa[0], fb[0])
+
+
+def test_adaptive_residual_checks_stop_like_fixed_sweeps(tds):
+    """Checks scheduled from the residual's decay stop at a residual below the
+    tolerance, and the state equals that many fixed sweeps bit for bit (a
+    check reads, it never writes)."""
+    scene = packed_scene(3000, 17, iters=2000, tol=1e-5)
+    g = tds.Scene(scene)
+    g.set_solver(2000, 1e-5, 0)
+    g.step(1)
+    st = g.stats()
+    adaptive = g.read_particles()
+    g.close()
+    assert st["residual"] <= 1e-5 and st["iterations"] < 2000
+    g = tds.Scene(scene)
+    g.set_solver(st["iterations"], 0.0, 10)
+    g.step(1)
+    fixed = g.read_particles()
+    g.close()
+    for k in ("x", "v", "w"):
+        assert np.array_equal(adaptive[k], fixed[k]), k
+    g = tds.Scene(scene)
+    g.set_solver(2000, 1e-5, 5)
+    g.step(1)
+    every5 = g.stats()
+    g.close()
+    assert every5["residual"] <= 1e-5
+    print("sweeps: adaptive", st["iterations"], "every 5", every5["iterations"])
