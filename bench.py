@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--pgs-blocks", type=int, default=0, help="solver CTAs (0: library default)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes (no untimed tuning before warm-up)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the learned and batched comparison forms of the default run")
     ap.add_argument("--unbatched", action="store_true",
                     help="batched workload: step the beds as separate scenes (the plain form)")
     ap.add_argument("--iters", type=int, default=0, help="override the sweeps per step")
@@ -700,6 +702,55 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
     return n * k / el, desc, k
 
 
+def learned_form(args, launch_cfg, stream) -> dict:
+    """The learned warm start on the headline's bed: an identical preparation
+    (same settle, launch shapes, approach and warm-up with the previous-step
+    warm start), then the same timed steps with the network trained on plain
+    solves of the small and bulldozing beds (weights shipped with the package)."""
+    import torch
+
+    from paper_2011_00459_gb300 import learned as LR
+    from paper_2011_00459_gb300 import scenes as S
+    from paper_2011_00459_gb300 import tds
+
+    work = make_workload(args, 0)
+    replay = {"shape": {k: launch_cfg[k] for k in ("pgs_blocks", "pgs_sync", "colour_blocks")}}
+    with torch.cuda.stream(stream):
+        sim, _ = prepare(args, work, tds, S, stream, replay=replay)
+        g = sim.g
+        g.set_mlp_weights(LR.load_weights())
+        g.set_warm_start(tds.WARM_LEARNED)
+        g.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.advance()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = g.stats()
+        g.close()
+    return {"warm_start": "learned (10-64-64-3 BF16 network)", "value": sim.n * args.steps / (ms * 1e-3),
+            "unit": UNIT, "ms_per_step": ms / args.steps,
+            "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
+            "final_residual": st["residual"], "steps": "the same steps as the headline (identical preparation)"}
+
+
+def batched_form(args, rank: int, world: int, local_rank: int) -> dict:
+    """The batched workload (256 beds in one graph-replayed batch) at the same
+    residual, timed like the headline."""
+    import copy
+
+    a = copy.copy(args)
+    a.workload, a.no_e2e, a.roofline_sweeps, a.no_cpu_baseline = "batched", True, 0, True
+    work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(a, rank, world, local_rank)
+    return {"workload": describe(work, a)["workload"], "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms / a.steps,
+            "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
+            "final_residual": st["residual"], "gpu_launches": int(launches)}
+
+
 def sample_scene(work) -> dict:
     """The scene the oracle samples: the bed itself, or the batch's bed of
     median size."""
@@ -782,6 +833,21 @@ def main():
             "ms_per_step": fixed["ms"] / args.steps,
             "contacts_per_step": fs["sum_contacts"] / max(1, fs["solved_steps"]),
             "phase_ms_per_step": phase(fs)}
+    if world == 1 and not args.no_forms and args.workload != "batched" and args.tol > 0:
+        import torch
+
+        result["forms"] = {"plain": {"warm_start": "previous step", "value": result["value"],
+                                     "ms_per_step": result["ms_per_step"],
+                                     "mean_sweeps": result["config"]["mean_sweeps"]}}
+        try:
+            result["forms"]["learned"] = learned_form(args, launch_cfg, torch.cuda.Stream())
+        except Exception as exc:  # a form that cannot run is reported, not fatal
+            result["forms"]["learned"] = {"error": repr(exc)}
+        if args.workload == "large":
+            try:
+                result["forms"]["batched"] = batched_form(args, rank, world, local_rank)
+            except Exception as exc:
+                result["forms"]["batched"] = {"error": repr(exc)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
 

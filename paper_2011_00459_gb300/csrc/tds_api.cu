@@ -17,8 +17,8 @@ int tds_launch_colouring(const DevPtrs &d, uint32_t n, uint32_t cap, int coop_bl
                          int coop_threads, cudaStream_t st);
 int tds_launch_bucketing(const DevPtrs &d, uint32_t cap, cudaStream_t st);
 int tds_launch_features(const DevPtrs &d, const StepConsts &k, int *surf, uint32_t ncols, uint32_t cap,
-                        cudaStream_t st);
-void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, cudaStream_t st);
+                        int compact, cudaStream_t st);
+void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, int compact, cudaStream_t st);
 size_t tds_mlp_packed_bytes();
 int tds_mlp_params();
 void tds_mlp_pack(const float *params, void *packed, cudaStream_t st);
@@ -401,6 +401,7 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.feat = c.take<float>(10 * (size_t)cap);
   d.sdirw = c.take<float4>(cap);
   d.c_flag = c.take<uint8_t>(cap);
+  d.new_idx = c.take<uint32_t>(cap);
   x.targ = c.take<float>(3 * (size_t)cap);
   x.surf = c.take<int>(L.ncols);
   x.packed = c.take<unsigned char>(tds_mlp_packed_bytes());
@@ -676,9 +677,12 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool c
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[2], s->st, evf));
   launches += tds_launch_colouring(d, s->L.n, s->L.cap, s->colour_blocks, 256, s->st);
   d.targ = s->recording ? s->x.targ : nullptr;
-  if (learned || s->recording) launches += tds_launch_features(d, s->k, s->x.surf, s->L.ncols, s->L.cap, s->st);
+  // without recording the network needs the features of the new contacts only
+  const int compact = learned && !s->recording;
+  if (learned || s->recording)
+    launches += tds_launch_features(d, s->k, s->x.surf, s->L.ncols, s->L.cap, compact, s->st);
   if (learned) {
-    tds_launch_learned(d, s->x.packed, s->L.cap, s->st);
+    tds_launch_learned(d, s->x.packed, s->L.cap, compact, s->st);
     launches += 1;
   }
   launches += tds_launch_bucketing(d, s->L.cap, s->st);

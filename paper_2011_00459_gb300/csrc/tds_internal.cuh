@@ -125,6 +125,7 @@ struct DevPtrs {
   float4 *sdirw;              // slip direction s and impulse scale W per contact
   float *targ;                // 3 targets per contact (recording)
   uint8_t *c_flag;            // 1 if the contact's key existed in the previous step
+  uint32_t *new_idx;          // learned warm start without recording: the contacts it starts
   float4 *p_il;               // impact stage, colour order: impulses (n, t1, t2, r.x)
   float4 *p_il2;              //   (r.y, r.z, G_n v* before the stage, normal target)
 };
@@ -133,7 +134,7 @@ struct DevPtrs {
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_IMPACTS = 13,
-       CTR_COUNT = 16 };
+       CTR_NEW = 14, CTR_COUNT = 16 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
 // ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
 // static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.

@@ -389,12 +389,31 @@ __device__ __forceinline__ float3 axis_tangent(float3 n) {
   return rsqrtf(dot(t, t)) * t;
 }
 
-// Features of every contact (owner order) at v* with the previous-step
-// impulses; also the slip direction s and the scale W for the outputs.
-__global__ void k_features(DevPtrs d, StepConsts k, const int *surf) {
+// The contacts without previous-step impulses, appended to new_idx (the
+// only ones the network starts when no training data are recorded).
+__global__ void k_new_contacts(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < nc;
+       base += gridDim.x * blockDim.x) {
+    const uint32_t c = base + lane;
+    const bool fresh = c < nc && d.c_flag[c] == 0;
+    const unsigned m = __ballot_sync(0xffffffffu, fresh);
+    uint32_t at = 0;
+    if (lane == 0 && m) at = atomicAdd(d.ctr + CTR_NEW, (uint32_t)__popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (fresh) d.new_idx[at + __popc(m & ((1u << lane) - 1u))] = c;
+  }
+}
+
+// Features at v* with the previous-step impulses, and the slip direction s
+// and scale W for the outputs: of every contact (row c of feat), or with
+// compact != 0 of the contacts listed in new_idx (row j for new_idx[j]).
+__global__ void k_features(DevPtrs d, StepConsts k, const int *surf, int compact) {
+  const uint32_t nrows = compact ? d.ctr[CTR_NEW] : d.ctr[CTR_NC];
   const float gh = sqrtf(k.g[0] * k.g[0] + k.g[1] * k.g[1] + k.g[2] * k.g[2]) * k.dt;
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+  for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x) {
+    const uint32_t c = compact ? d.new_idx[row] : row;
     const uint2 ab = d.c_ab[c];
     const bool dyn = (ab.y & TDS_STATIC) == 0u;
     const float4 rn = d.c_rn[c], rq = d.c_rq[c];
@@ -426,7 +445,7 @@ __global__ void k_features(DevPtrs d, StepConsts k, const int *surf) {
     float depth = 0.f;
     if (G.cf > 0) depth = (unordered(surf[column_of(G, P.x, P.y)]) - P.z) / dbar;
     const uint32_t sid = ab.y & ~TDS_STATIC;
-    float *F = d.feat + (size_t)c * 10;
+    float *F = d.feat + (size_t)row * 10;
     F[0] = dot(n, dv) / gh;
     F[1] = delta / dbar;
     F[2] = l0.x / W;
@@ -437,7 +456,7 @@ __global__ void k_features(DevPtrs d, StepConsts k, const int *surf) {
     F[7] = dyn ? (float)d.inc_cnt[ab.y] : 0.f;
     F[8] = depth;
     F[9] = dyn ? 0.f : (sid >= 1u + G.nwall ? 2.f : 1.f);
-    d.sdirw[c] = make_float4(s.x, s.y, s.z, W);
+    d.sdirw[row] = make_float4(s.x, s.y, s.z, W);
   }
 }
 
@@ -446,12 +465,12 @@ __global__ void k_features(DevPtrs d, StepConsts k, const int *surf) {
 // those, which already start it near its solution):
 // Lambda_n = W y0, Lambda_t = W (y1 s + y2 n x s), no rolling impulse; all
 // projected into the bounds (normal >= -f_c, Coulomb disk).
-__global__ void __launch_bounds__(256) k_learned(DevPtrs d, const Packed *gP) {
+__global__ void __launch_bounds__(256) k_learned(DevPtrs d, const Packed *gP, int compact) {
   __shared__ Packed P;
   for (int i = threadIdx.x; i < (int)(sizeof(Packed) / 4); i += blockDim.x)
     reinterpret_cast<uint32_t *>(&P)[i] = reinterpret_cast<const uint32_t *>(gP)[i];
   __syncthreads();
-  const uint32_t nc = d.ctr[CTR_NC];
+  const uint32_t nc = compact ? d.ctr[CTR_NEW] : d.ctr[CTR_NC];  // rows of feat
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   const uint32_t warps = (blockDim.x >> 5) * gridDim.x;
   for (uint32_t tile = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile * 16 < nc; tile += warps) {
@@ -461,10 +480,12 @@ __global__ void __launch_bounds__(256) k_learned(DevPtrs d, const Packed *gP) {
     if (t != 0) continue;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const uint32_t c = tile * 16 + g + 8 * h;
-      if (c >= nc || d.c_flag[c]) continue;
+      const uint32_t row = tile * 16 + g + 8 * h;
+      if (row >= nc) continue;
+      const uint32_t c = compact ? d.new_idx[row] : row;
+      if (d.c_flag[c]) continue;
       const float y0 = h ? f.y[2] : f.y[0], y1 = h ? f.y[3] : f.y[1], y2 = h ? y2b : y2a;
-      const float4 sw = d.sdirw[c], rn = d.c_rn[c], rq = d.c_rq[c];
+      const float4 sw = d.sdirw[row], rn = d.c_rn[c], rq = d.c_rq[c];
       const float2 rm = d.c_rm[c];
       const float3 n = f3(rn), s = f3(sw);
       const float W = sw.w;
@@ -483,8 +504,10 @@ __global__ void __launch_bounds__(256) k_learned(DevPtrs d, const Packed *gP) {
 
 }  // namespace
 
+// compact != 0: features of the new contacts only (listed first), for the
+// learned warm start when no training data are recorded.
 int tds_launch_features(const DevPtrs &d, const StepConsts &k, int *surf, uint32_t ncols, uint32_t cap,
-                        cudaStream_t st) {
+                        int compact, cudaStream_t st) {
   int launches = 1;
   if (ncols > 0) {
     k_columns_clear<<<(ncols + 255) / 256, 256, 0, st>>>(ncols, surf);
@@ -493,14 +516,19 @@ int tds_launch_features(const DevPtrs &d, const StepConsts &k, int *surf, uint32
   }
   unsigned blocks = (cap + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_features<<<blocks, 256, 0, st>>>(d, k, surf);
+  if (compact) {
+    cudaMemsetAsync(d.ctr + CTR_NEW, 0, sizeof(uint32_t), st);
+    k_new_contacts<<<blocks, 256, 0, st>>>(d);
+    launches += 1;
+  }
+  k_features<<<blocks, 256, 0, st>>>(d, k, surf, compact);
   return launches;
 }
-void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, cudaStream_t st) {
+void tds_launch_learned(const DevPtrs &d, const void *packed, uint32_t cap, int compact, cudaStream_t st) {
   unsigned blocks = (cap + 127) / 128;
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks == 0) blocks = 1;
-  k_learned<<<blocks, 256, 0, st>>>(d, static_cast<const Packed *>(packed));
+  k_learned<<<blocks, 256, 0, st>>>(d, static_cast<const Packed *>(packed), compact);
 }
 
 size_t tds_mlp_packed_bytes() { return (sizeof(Packed) + 255) & ~(size_t)255; }

@@ -8,6 +8,8 @@ contacts that have no previous-step impulses, so those are the samples kept.
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 from . import scenes as S
@@ -112,3 +114,42 @@ def train(tds, X, T, epochs: int = 30, batch: int = 8192, lr: float = 2e-3, seed
         if report:
             log(f"learned: epoch {e}: standardised loss {loss / len(X):.4g}")
     return fold(net.host_params(), mx, sx, mt, st, tds).astype(np.float32)
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "warmstart_mlp.npz")
+
+
+def load_weights(path: str = WEIGHTS) -> np.ndarray:
+    """Trained parameters shipped with the package (written by ``main``)."""
+    with np.load(path) as f:
+        return np.asarray(f["params"], np.float32)
+
+
+def main(argv=None) -> int:
+    """Collect samples, train on the GPU and write the parameters:
+    ``python -m paper_2011_00459_gb300.learned --samples 400000 --out PATH``."""
+    import argparse
+    import time
+
+    from . import build, tds
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--samples", type=int, default=400_000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=WEIGHTS)
+    a = ap.parse_args(argv)
+    build.build()
+    t0 = time.time()
+    X, T = collect(tds, samples=a.samples, seed=a.seed, log=print)
+    params = train(tds, X, T, epochs=a.epochs, seed=a.seed, log=print)
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    np.savez(a.out, params=params, samples=len(X), epochs=a.epochs, seed=a.seed,
+             sources="new contacts of plain solves (residual 1e-5) of the small and bulldozing beds dug by "
+                     "their blades")
+    print(f"wrote {a.out}: {len(X)} samples, {time.time() - t0:.0f} s")
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

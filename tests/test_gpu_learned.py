@@ -176,3 +176,27 @@ def test_learned_warm_start_reaches_the_same_residual(tds):
         sweeps[name] = its
     print("sweeps to 1e-4:", sweeps)
     assert np.mean(sweeps["learned"]) <= 2.0 * np.mean(sweeps["previous-step"])
+
+
+def test_learned_steps_equal_with_and_without_recording(tds):
+    """Without recording the network runs on the new contacts only (their
+    features compacted first); with recording on every contact. Each row's
+    prediction depends on its own features alone, so the steps are identical."""
+    flat = rand_params(tds, 9, scale=0.3)
+    out = []
+    for record in (False, True):
+        scene = packed_scene(2500, 19, iters=30)
+        g = tds.Scene(scene)
+        g.set_mlp_weights(flat)
+        g.set_warm_start(tds.WARM_LEARNED)
+        g.set_recording(record)
+        path = scene["tool"]
+        for k in range(4):
+            t = dict(path)
+            t["pos"] = tuple(np.asarray(path["pos"]) + np.asarray(path["vel"]) * k / 60.0)
+            g.set_tool_pose(t)
+            g.step(1)
+        out.append(g.read_particles())
+        g.close()
+    for key in ("x", "v", "w"):
+        assert np.array_equal(out[0][key], out[1][key]), key
