@@ -232,11 +232,11 @@ static int detect(const orc_params *P, int n, const double *x, const double *r,
     xf[4 * i + 3] = (float)r[i];
     if (r[i] > rmax) rmax = r[i];
   }
-  /* particle-particle */
+  /* particle-particle (radius 0: a dormant reserve slot, never in contact) */
   if (brute) {
     for (int a = 0; a < n; ++a)
       for (int b = a + 1; b < n; ++b)
-        if (pp_touch(xf[4 * a], xf[4 * a + 1], xf[4 * a + 2], xf[4 * a + 3], xf[4 * b],
+        if (r[a] > 0.0 && r[b] > 0.0 && pp_touch(xf[4 * a], xf[4 * a + 1], xf[4 * a + 2], xf[4 * a + 3], xf[4 * b],
                      xf[4 * b + 1], xf[4 * b + 2], xf[4 * b + 3], cohesive))
           kl_push(L, ((uint64_t)a << 32) | (uint64_t)b);
   } else if (n > 0) {
@@ -244,36 +244,42 @@ static int detect(const orc_params *P, int n, const double *x, const double *r,
      * found in the 27 surrounding cells, and the predicate decides. */
     double cell = 2.1 * rmax;
     if (!(cell > 0.0)) cell = 1.0;
-    double lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
-    for (int i = 1; i < n; ++i)
+    double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+    for (int i = 0; i < n; ++i)
       for (int k = 0; k < 3; ++k) {
+        if (!(r[i] > 0.0)) continue;
         if (x[3 * i + k] < lo[k]) lo[k] = x[3 * i + k];
         if (x[3 * i + k] > hi[k]) hi[k] = x[3 * i + k];
       }
+    if (!(lo[0] <= hi[0])) for (int k = 0; k < 3; ++k) lo[k] = hi[k] = 0.0;
     int64_t dim[3];
     for (int k = 0; k < 3; ++k) dim[k] = (int64_t)floor((hi[k] - lo[k]) / cell) + 3;
     cell_entry *E = (cell_entry *)malloc(sizeof(cell_entry) * n);
     if (!E) { free(xf); return -2; }
     int64_t (*ci)[3] = malloc(sizeof(int64_t[3]) * n);
     if (!ci) { free(E); free(xf); return -2; }
+    int na = 0;  /* active particles in E */
     for (int i = 0; i < n; ++i) {
+      if (!(r[i] > 0.0)) continue;
       for (int k = 0; k < 3; ++k) ci[i][k] = (int64_t)floor((x[3 * i + k] - lo[k]) / cell) + 1;
-      E[i].cell = (ci[i][2] * dim[1] + ci[i][1]) * dim[0] + ci[i][0];
-      E[i].idx = i;
+      E[na].cell = (ci[i][2] * dim[1] + ci[i][1]) * dim[0] + ci[i][0];
+      E[na].idx = i;
+      ++na;
     }
-    qsort(E, n, sizeof(cell_entry), cmp_cell);
+    qsort(E, na, sizeof(cell_entry), cmp_cell);
     for (int a = 0; a < n; ++a) {
+      if (!(r[a] > 0.0)) continue;
       for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy)
           for (int dx = -1; dx <= 1; ++dx) {
             int64_t c = ((ci[a][2] + dz) * dim[1] + (ci[a][1] + dy)) * dim[0] + ci[a][0] + dx;
             /* lower bound of cell c */
-            int lo_i = 0, hi_i = n;
+            int lo_i = 0, hi_i = na;
             while (lo_i < hi_i) {
               int mid = (lo_i + hi_i) / 2;
               if (E[mid].cell < c) lo_i = mid + 1; else hi_i = mid;
             }
-            for (int m = lo_i; m < n && E[m].cell == c; ++m) {
+            for (int m = lo_i; m < na && E[m].cell == c; ++m) {
               int b = E[m].idx;
               if (b <= a) continue;
               if (pp_touch(xf[4 * a], xf[4 * a + 1], xf[4 * a + 2], xf[4 * a + 3], xf[4 * b],
@@ -288,6 +294,7 @@ static int detect(const orc_params *P, int n, const double *x, const double *r,
   /* particle-heightfield and particle-box */
   for (int a = 0; a < n; ++a) {
     float px = xf[4 * a], py = xf[4 * a + 1], pz = xf[4 * a + 2], ra = xf[4 * a + 3];
+    if (!(r[a] > 0.0)) continue;
     if (P->hf_nx > 0) {
       hf_tri t;
       float s = hf_signed_distance(P, px, py, pz, &t);
@@ -766,6 +773,7 @@ static int contact_features(const orc_params *P, int n, const double *x, const d
     if (!surf) { free(Z); return -1; }
     for (int q = 0; q < ncx * ncy; ++q) surf[q] = -INFINITY;
     for (int i = 0; i < n; ++i) {
+      if (!(r[i] > 0.0)) continue;  /* dormant */
       int col = column_of(P, f, (float)x[3 * i], (float)x[3 * i + 1], ncx, ncy);
       float top = (float)x[3 * i + 2] + (float)r[i];
       if (top > surf[col]) surf[col] = top;
@@ -884,6 +892,7 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
   keys = (uint64_t *)malloc(sizeof(uint64_t) * (cap + 1));
   if (!M.m_inv || !M.I_inv || !keys) { rc = -2; goto done; }
   for (int i = 0; i < n; ++i) {
+    if (!(r[i] > 0.0)) { M.m_inv[i] = M.I_inv[i] = 0.0; continue; }  /* dormant */
     double m = P->density * 4.0 / 3.0 * ORC_PI * r[i] * r[i] * r[i];
     M.m_inv[i] = 1.0 / m;
     M.I_inv[i] = 1.0 / (0.4 * m * r[i] * r[i]);
@@ -923,7 +932,8 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
   free(v0);
   /* 2. p = M v_n + h f: v^* = v_n + h g (gravity is the only external force) */
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < 3; ++k) v[3 * i + k] += h * P->gravity[k];
+    if (r[i] > 0.0)
+      for (int k = 0; k < 3; ++k) v[3 * i + k] += h * P->gravity[k];
   /* 3. warm start: previous impulses by key, Lambda_t re-projected onto the
    *    new tangent plane, all clamped into the new bounds (v += M^-1 G^T
    *    lambda_0 follows the impact stage below) */
@@ -1012,7 +1022,9 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     }
   }
   /* 7. x_{n+1} = x_n + h v_{n+1} */
-  for (int i = 0; i < 3 * n; ++i) x[i] += h * v[i];
+  for (int i = 0; i < n; ++i)
+    if (r[i] > 0.0)
+      for (int k = 0; k < 3; ++k) x[3 * i + k] += h * v[3 * i + k];
   /* outputs in ascending key order */
   st->n_contacts = nc;
   for (int k = 0; k < nc; ++k) {
