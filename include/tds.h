@@ -146,6 +146,7 @@ typedef struct {
   uint64_t sweep_contacts_pp, sweep_contacts_static, sum_contacts, solved_steps;
   uint32_t colour_rounds;      /* rounds of the parallel greedy colouring, last step */
   uint32_t impacts;            /* contacts treated as impacts, last step */
+  uint32_t spawned;            /* particles the active zones created, last step */
 } tds_step_stats;
 
 /* Bytes of device workspace a scene with this description needs. */
@@ -328,6 +329,51 @@ tds_status tds_coarse_grain(tds_scene *s, const tds_grid *grid, int32_t kernel, 
                             float *u);
 tds_status tds_advect_fluid(const tds_grid *grid, const float *u, const float *rho_f, const float *source,
                             float dt, float *rho_out, void *stream);
+
+/* ---- active zone: cutting the terrain into particles ----------------------------
+ * Section "Mesoscale model": a cutting edge moving through the terrain
+ * carries a wedge-shaped active zone bounded by the separation plane (the
+ * blade face), the failure plane from the edge to the free surface, rising
+ * ahead of the blade at theta = pi/2 - (phi + beta)/2 above the horizontal
+ * (Eq. failure_plane; phi the soil's internal friction angle, beta the
+ * separation plane's inclination to the horizontal), and the ends of the edge;
+ * the terrain it overlaps turns into particles.
+ * After each step, for a scene with a cutter on its tool: every heightfield
+ * node whose point on the failure plane lies within the edge's length and at
+ * least spawn_radius ahead of the blade, and whose height is above it, is
+ * lowered onto the failure plane; bank_density times the removed height times
+ * the cell area becomes the node's pending mass. A node cut this step then
+ * places particles of radius spawn_radius at rest in its liberated column
+ * (from its height up to the highest it has been), j-th at
+ * height + spawn_radius (1 + 2j), first fit: a position is taken when no
+ * active particle overlaps it (FP32 test) and the pending mass pays for a
+ * particle (particle density); nodes in index order, each particle taking the
+ * scene's next dormant slot (radius 0, in increasing id order). Mass that finds
+ * no place or slot stays pending. Not modelled: fluidized mass, the reverse
+ * conversion (deposition, gap filling). All in FP32 on the device, after the
+ * position update, on the scene's stream.
+ * Dormant slots: particles created with radius 0 are reserve slots (no
+ * contacts, no gravity, no mass) that the cut fills; tds_read_radii tells them
+ * apart. */
+typedef struct {
+  float edge[3];        /* a point of the cutting edge, tool frame [m] */
+  float dir[3];         /* direction along the edge, tool frame (normalised) */
+  float length;         /* edge length [m]; 0 removes the cutter */
+  float normal[3];      /* separation-plane normal pointing ahead into the soil, tool frame */
+  float phi;            /* internal friction angle of the soil [rad] */
+  float bank_density;   /* mass density of the resting terrain [kg/m^3] */
+  float spawn_radius;   /* radius of the new particles [m]: <= the largest radius at creation,
+                           <= half the heightfield cell */
+} tds_cutter;
+tds_status tds_set_cutter(tds_scene *s, uint32_t scene, const tds_cutter *cutter);
+
+/* The scene's current heightfield heights and pending (cut, not yet
+ * particle) mass per node [kg], (hf_nx+1)*(hf_ny+1) floats each (either may
+ * be NULL). Waits. */
+tds_status tds_read_heightfield(tds_scene *s, uint32_t scene, float *heights, float *pending, uint32_t count);
+
+/* Radii of all particles by id (0: a dormant slot). Waits. */
+tds_status tds_read_radii(tds_scene *s, float *r, uint32_t n);
 
 /* ---- launch shapes ------------------------------------------------------------
  * Knobs of the GPU schedule (the paper, a CPU method, has none). Results do

@@ -20,9 +20,14 @@ Readings:
 * a node cut this step places particles of one radius r_s in its liberated
   column, from its new height up to the highest it has been: the j-th position
   is z_f + r_s (1 + 2j), taken first fit while it stays below that top and the
-  pending mass pays for a particle, unless an active particle overlaps it
-  ((dx^2 + dy^2) + dz^2 < (r_s + r)^2 in FP32, positions after the step's
-  update); nodes are at least 2 r_s apart, so new particles never overlap each
+  pending mass pays for a particle, unless it lies closer than r_s to the
+  plane of a terrain triangle around the node (heights after the step's cut:
+  every such plane passes through the node, so the distance is
+  cell (z - z_f) / den, den the largest sqrt((cell^2 + A^2) + B^2) over those
+  triangles, A and B a triangle's height steps along its legs; a sphere of
+  radius r_s <= cell / 2 centred above the node reaches no other triangle) or
+  an active particle overlaps it ((dx^2 + dy^2) + dz^2 < (r_s + r)^2 in FP32,
+  positions after the step's update); nodes are at least 2 r_s apart, so new particles never overlap each
   other; they start at rest; the rest stays pending at the node;
 * new particles take dormant particles (radius 0) of the scene in increasing id
   order, nodes in index order, each node's accepted positions in order; with
@@ -91,6 +96,27 @@ def wedge(tool: dict, cutter: dict, density: float) -> dict | None:
             "theta": theta}
 
 
+def _node_den(h, cell):
+    """Per node, the largest FP32 sqrt((cell^2 + A^2) + B^2) over the
+    heightfield triangles that have the node as a corner. Triangles of cell
+    (a, b): lower with corners (a, b), (a+1, b), (a, b+1), A and B the height
+    steps from the first corner to the second and third; upper with corners
+    (a+1, b+1), (a, b+1), (a+1, b), likewise."""
+    ny1, nx1 = h.shape
+    c2 = cell * cell
+    lo_a, lo_b = h[:-1, 1:] - h[:-1, :-1], h[1:, :-1] - h[:-1, :-1]  # lower triangle of each cell
+    up_a, up_b = h[1:, :-1] - h[1:, 1:], h[:-1, 1:] - h[1:, 1:]  # upper triangle of each cell
+    lo = np.sqrt((c2 + lo_a * lo_a) + lo_b * lo_b).astype(np.float32)
+    up = np.sqrt((c2 + up_a * up_a) + up_b * up_b).astype(np.float32)
+    den = np.full((ny1, nx1), cell, np.float32)
+    # lower (a, b) has corners (a, b), (a+1, b), (a, b+1); upper (a, b) has
+    # (a+1, b+1), (a, b+1), (a+1, b); offsets below are (row b, column a)
+    for t, (dj, di) in ((lo, (0, 0)), (lo, (0, 1)), (lo, (1, 0)), (up, (1, 1)), (up, (1, 0)), (up, (0, 1))):
+        sub = den[dj:dj + ny1 - 1, di:di + nx1 - 1]
+        np.maximum(sub, t, out=sub)
+    return den
+
+
 def cut_and_spawn(hf: dict, pending, top, W: dict, x, r):
     """One step's cut and conversion. hf: the scene's heightfield dict (heights
     "h" as of this step); pending, top: per-node pending mass and highest
@@ -121,6 +147,7 @@ def cut_and_spawn(hf: dict, pending, top, W: dict, x, r):
     pend = np.where(inside, pend + lib, pend).astype(np.float32)
     h = np.where(inside, zf, h).astype(np.float32)
     # conversion at the nodes cut this step
+    den = _node_den(h, f32(hf["cell"]))
     xf = np.asarray(x, np.float32).reshape(-1, 3)
     rf = np.asarray(r, np.float32).reshape(-1)
     active = np.nonzero(rf > 0)[0]
@@ -141,6 +168,8 @@ def cut_and_spawn(hf: dict, pending, top, W: dict, x, r):
             z = z0 + (rs + two_rs * f32(q))
             if z + rs > top[j, i] or rem < ms:
                 break
+            if (cell * (z - z0)) / den[j, i] < rs:  # too close to the terrain around the node
+                continue
             blocked = False
             if tree is not None:
                 for k in tree.query_ball_point((float(x0), float(y0), float(z)), reach):

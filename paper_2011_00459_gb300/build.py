@@ -16,7 +16,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libtds.so")
 
 SOURCES = ["tds_api.cu", "tds_contacts.cu", "tds_colour.cu", "tds_solve.cu", "tds_scan.cu",
-           "tds_noalloc.cu", "tds_mlp.cu", "tds_aggregate.cu", "tds_fields.cu"]
+           "tds_noalloc.cu", "tds_mlp.cu", "tds_aggregate.cu", "tds_fields.cu", "tds_cut.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kAggThreads) k_agg_first(DevPtrs d, uint32_t n
     double val[kFirst] = {};
     if (i < hi) {
       const float4 p = d.pos[i];
-      z = zone_of(sz, nz, d.sid[i], p);
+      z = p.w > 0.0f ? zone_of(sz, nz, d.sid[i], p) : -1;  // dormant slots belong to no zone
       zone_id[i] = z < 0 ? 0xFF : (uint8_t)z;
       if (z >= 0) {
         const float4 v = d.pv[2 * (size_t)i];

@@ -3,6 +3,7 @@
 // per-step orchestration of the kernels on the scene's stream (optionally
 // replayed as CUDA graphs), and the read calls. A scene is a batch of one.
 #include <cmath>
+#include <math.h>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -33,6 +34,7 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
 cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
                               int blocks, cudaStream_t st);
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
+int tds_launch_cut(const DevPtrs &d, const StepConsts &k, float *heights, uint32_t nh, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 int tds_pgs_setup(int *threads);
 int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, uint32_t nz, uint8_t *zone_id,
@@ -94,11 +96,14 @@ struct Carver {
 struct SceneHost {
   uint32_t off, n;                  // particle ids [off, off + n)
   std::vector<float> walls, tools;  // 10 floats per box
+  bool has_cutter = false;
+  tds_cutter cutter{};
   float pos[3] = {0, 0, 0}, quat[4] = {1, 0, 0, 0}, vel[3] = {0, 0, 0}, angvel[3] = {0, 0, 0};
 };
 
 struct Layout {
   uint32_t S = 0, n = 0, cap = 0, ncells = 0, ntiles = 0, nheights = 1, nboxes = 0, ncols = 0;
+  float rmax = 0.f;
   int gnx = 1, gny = 1, gnz = 1;
   float cell = 1.f;
   std::vector<SceneGeo> geo;
@@ -122,14 +127,14 @@ struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
 // arguments that the host settings select.
 struct GraphKey {
   int use_prev = -1, warm = -1, recording = -1, timing = -1;
-  int pgs_blocks = -1, pgs_sync = -1, colour_blocks = -1;
+  int pgs_blocks = -1, pgs_sync = -1, colour_blocks = -1, cutter = -1;
   uint32_t max_iters = 0, every = 0, impact_iters = 0;
   float tol = -1.f, restitution = -1.f, impact_speed = -1.f;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
            pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && colour_blocks == o.colour_blocks &&
            max_iters == o.max_iters && every == o.every && tol == o.tol && impact_iters == o.impact_iters &&
-           restitution == o.restitution && impact_speed == o.impact_speed;
+           restitution == o.restitution && impact_speed == o.impact_speed && cutter == o.cutter;
   }
 };
 
@@ -163,6 +168,7 @@ struct tds_scene {
   bool geo_dirty = true;
   int pgs_blocks = 1, colour_blocks = 1;
   int pgs_sync = 1;       // solver: 1 neighbour synchronisation, 0 grid barrier
+  bool any_cutter = false;
   int max_pgs_blocks = 1, max_colour_blocks = 1;
   uint64_t steps = 0;
   tds_status latched = TDS_OK;
@@ -202,9 +208,9 @@ tds_status validate(const tds_scene_desc *d) {
       !std::isfinite(d->impact_speed))
     return fail(TDS_ERR_INVALID_ARG, "restitution must be in [0, 1] and impact_speed >= 0");
   for (uint32_t i = 0; i < d->n; ++i)
-    if (!(d->radius[i] > 0.f) || !std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) ||
-        !std::isfinite(d->z[i]))
-      return fail(TDS_ERR_INVALID_ARG, "radii must be > 0 and positions finite");
+    if (!(d->radius[i] >= 0.f) || !std::isfinite(d->radius[i]) || !std::isfinite(d->x[i]) ||
+        !std::isfinite(d->y[i]) || !std::isfinite(d->z[i]))
+      return fail(TDS_ERR_INVALID_ARG, "radii must be >= 0 (0: dormant slot) and positions finite");
   return TDS_OK;
 }
 
@@ -228,6 +234,10 @@ tds_status validate_batch(const tds_scene_desc *descs, uint32_t count) {
                   "solver settings, warm_start, contacts_per_particle and the impact stage");
   }
   if (total >= 0x7FFFFFFFull) return fail(TDS_ERR_INVALID_ARG, "too many particles in the batch");
+  bool active = false;
+  for (uint32_t q = 0; q < count && !active; ++q)
+    for (uint32_t i = 0; i < descs[q].n && !active; ++i) active = descs[q].radius[i] > 0.f;
+  if (!active) return fail(TDS_ERR_INVALID_ARG, "at least one particle needs a radius > 0");
   return TDS_OK;
 }
 
@@ -241,12 +251,27 @@ void scene_domain(const tds_scene_desc *d, float cell, float lo[3], float hi[3])
     return;
   }
   const float *xs[3] = {d->x, d->y, d->z};
-  for (int a = 0; a < 3; ++a) {
-    lo[a] = hi[a] = xs[a][0];
-    for (uint32_t i = 1; i < d->n; ++i) {
-      lo[a] = std::fmin(lo[a], xs[a][i]);
-      hi[a] = std::fmax(hi[a], xs[a][i]);
+  bool any = false;  // active particles only: dormant slots may sit anywhere
+  for (uint32_t i = 0; i < d->n; ++i) {
+    if (!(d->radius[i] > 0.f)) continue;
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = any ? std::fmin(lo[a], xs[a][i]) : xs[a][i];
+      hi[a] = any ? std::fmax(hi[a], xs[a][i]) : xs[a][i];
     }
+    any = true;
+  }
+  if (!any) {  // no active particle yet: the heightfield's extent, or the origin
+    lo[0] = d->hf_nx ? d->hf_x0 : 0.f;
+    lo[1] = d->hf_nx ? d->hf_y0 : 0.f;
+    hi[0] = d->hf_nx ? d->hf_x0 + d->hf_nx * d->hf_cell : 1.f;
+    hi[1] = d->hf_nx ? d->hf_y0 + d->hf_ny * d->hf_cell : 1.f;
+    lo[2] = 0.f;
+    hi[2] = 1.f;
+    if (d->hf_nx)
+      for (uint32_t q = 0; q < (d->hf_nx + 1) * (d->hf_ny + 1); ++q) {
+        lo[2] = std::fmin(lo[2], d->hf_heights[q]);
+        hi[2] = std::fmax(hi[2], d->hf_heights[q] + 1.f);
+      }
   }
   for (uint32_t w = 0; w < d->n_walls; ++w) {  // the walls bound the bed
     const float *b = d->walls + 10 * w;
@@ -276,6 +301,7 @@ Layout plan(const tds_scene_desc *descs, uint32_t S) {
   }
   if (cap > 0x7FFFFFF0ull) cap = 0x7FFFFFF0ull;
   L.cap = (uint32_t)cap;
+  L.rmax = rmax;
   L.ntiles = (L.cap + TDS_TILE - 1) / TDS_TILE;
   // cells wider than any reach (2 r_max plus the cohesive band), with margin
   L.cell = 2.0f * rmax * 1.025f * 1.02f;
@@ -314,6 +340,7 @@ Layout plan(const tds_scene_desc *descs, uint32_t S) {
     boff += G.nbox;
     G.mu_t = d.mu_t; G.mu_tool = d.mu_tool; G.mu_r = d.mu_r;
     G.pid0 = pid0;
+    G.npart = d.n;
     pid0 += d.n;
     // surface columns of the learned warm start: heightfield cells grouped
     // cf x cf, cf the smallest integer with cf * cell >= 4 r_max of the scene
@@ -342,9 +369,9 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.pos2 = c.take<float4>(n); d.pv2 = c.take<float4>(2 * (size_t)n);
   d.pid2 = c.take<uint32_t>(n); d.sid2 = c.take<uint32_t>(n);
   d.cell_of = c.take<uint32_t>(n);
-  d.cell_count = c.take<uint32_t>(L.ncells + 1);
-  d.cell_start = c.take<uint32_t>(L.ncells + 1);
-  d.cell_cursor = c.take<uint32_t>(L.ncells);
+  d.cell_count = c.take<uint32_t>(L.ncells + 2);  // + the trailing cell of dormant slots
+  d.cell_start = c.take<uint32_t>(L.ncells + 2);
+  d.cell_cursor = c.take<uint32_t>(L.ncells + 1);
   d.perm = c.take<uint32_t>(n);
   d.cnt = c.take<uint32_t>(n + 1);
   d.cstart = c.take<uint32_t>(n + 1);
@@ -391,17 +418,26 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.bar = c.take<uint32_t>(2);
   d.prog = c.take<uint32_t>(kProgStride * (size_t)pgs_blocks);
   d.rng = c.take<uint32_t>(2 * (size_t)pgs_blocks);
-  size_t m = L.ncells;
+  size_t m = L.ncells + 1;
   if (m < n) m = n;
   if (m < (size_t)TDS_NBUCKETS * L.ntiles) m = (size_t)TDS_NBUCKETS * L.ntiles;
+  if (m < (size_t)L.nheights) m = L.nheights;
   d.scan_tmp = c.take<uint32_t>(tds_scan_tmp_words((uint32_t)m));
-  d.stage = c.take<float>(9 * (size_t)n);
+  d.stage = c.take<float>(10 * (size_t)n);
   d.tool_out = c.take<float>(6 * (size_t)L.S);
   d.tool_acc = c.take<double>(6 * (size_t)L.S);
   d.feat = c.take<float>(10 * (size_t)cap);
   d.sdirw = c.take<float4>(cap);
   d.c_flag = c.take<uint8_t>(cap);
   d.new_idx = c.take<uint32_t>(cap);
+  d.hf_pend = c.take<float>(L.nheights);
+  d.hf_top = c.take<float>(L.nheights);
+  d.hf_scene = c.take<uint32_t>(L.nheights);
+  d.hf_cnt = c.take<uint32_t>((size_t)L.nheights + 1);
+  d.hf_rank = c.take<uint32_t>((size_t)L.nheights + 1);
+  d.dorm_rank = c.take<uint32_t>((size_t)n + 1);
+  d.dorm_list = c.take<uint32_t>(n);
+  d.slot_of_pid = c.take<uint32_t>(n);
   x.targ = c.take<float>(3 * (size_t)cap);
   x.surf = c.take<int>(L.ncols);
   x.packed = c.take<unsigned char>(tds_mlp_packed_bytes());
@@ -426,6 +462,59 @@ void set_box(BoxF &B, const double R[9], const double c[3], const float h[3], in
   for (int i = 0; i < 9; ++i) B.R[i] = (float)R[i];
   for (int i = 0; i < 3; ++i) { B.c[i] = (float)c[i]; B.h[i] = h[i]; }
   B.is_tool = is_tool;
+}
+
+double norm3d(const double a[3]) { return std::sqrt((a[0] * a[0] + a[1] * a[1]) + a[2] * a[2]); }
+
+// The active-zone wedge of scene s's cutter on the tool pose (rotation RT),
+// in FP64 then rounded: edge start e0 = p_T + R_T edge, edge direction u and
+// blade normal ns (normalised), beta = the separation plane's inclination to
+// the horizontal = acos |ns_z|, theta = pi/2 - (phi + beta)/2 (Eq.
+// failure_plane), the failure plane through the edge spanned by u and
+// d = (cos theta f, sin theta) with f the horizontal direction of ns; its
+// normal nf = d x u points up.
+void compose_wedge(tds_scene *S, uint32_t s, const double RT[9]) {
+  const SceneHost &h = S->scenes[s];
+  SceneGeo &G = S->L.geo[s];
+  G.cut_on = 0;
+  if (!h.has_cutter || !(h.cutter.length > 0.f)) return;
+  const tds_cutter &c = h.cutter;
+  double e[3], u[3], ns[3];
+  for (int i = 0; i < 3; ++i) {
+    e[i] = (double)h.pos[i] + ((RT[3 * i] * (double)c.edge[0] + RT[3 * i + 1] * (double)c.edge[1]) +
+                               RT[3 * i + 2] * (double)c.edge[2]);
+    u[i] = (RT[3 * i] * (double)c.dir[0] + RT[3 * i + 1] * (double)c.dir[1]) + RT[3 * i + 2] * (double)c.dir[2];
+    ns[i] = (RT[3 * i] * (double)c.normal[0] + RT[3 * i + 1] * (double)c.normal[1]) +
+            RT[3 * i + 2] * (double)c.normal[2];
+  }
+  const double lu = norm3d(u), ln = norm3d(ns);
+  for (int i = 0; i < 3; ++i) { u[i] /= lu; ns[i] /= ln; }
+  const double beta = std::acos(std::fmin(1.0, std::fabs(ns[2])));
+  const double theta = 0.5 * M_PI - 0.5 * ((double)c.phi + beta);
+  const double fh = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1]);
+  if (fh < 1e-9) return;
+  const double f[2] = {ns[0] / fh, ns[1] / fh};
+  const double dd[3] = {std::cos(theta) * f[0], std::cos(theta) * f[1], std::sin(theta)};
+  double nf[3] = {dd[1] * u[2] - dd[2] * u[1], dd[2] * u[0] - dd[0] * u[2], dd[0] * u[1] - dd[1] * u[0]};
+  if (nf[2] < 0.0) for (int i = 0; i < 3; ++i) nf[i] = -nf[i];
+  const double lf = norm3d(nf);
+  for (int i = 0; i < 3; ++i) nf[i] /= lf;
+  if (std::fabs(nf[2]) < 1e-6) return;
+  const double rs = (double)c.spawn_radius;
+  const double m = S->desc.density * 4.0 / 3.0 * M_PI * rs * rs * rs;
+  for (int i = 0; i < 3; ++i) {
+    G.e0[i] = (float)e[i];
+    G.u[i] = (float)u[i];
+    G.ns[i] = (float)ns[i];
+    G.nf[i] = (float)nf[i];
+  }
+  G.cut_len = c.length;
+  G.rho_b = c.bank_density;
+  G.rs = c.spawn_radius;
+  G.ms = (float)m;
+  G.inv_m = (float)(1.0 / m);
+  G.inv_I = (float)(1.0 / (0.4 * m * rs * rs));
+  G.cut_on = 1;
 }
 
 // World-frame boxes of scene s for its current tool pose: walls as given,
@@ -462,6 +551,7 @@ void compose_boxes(tds_scene *S, uint32_t s) {
     G.tv[i] = h.vel[i];
     G.tw[i] = h.angvel[i];
   }
+  compose_wedge(S, s, RT);
   S->geo_dirty = true;
 }
 
@@ -598,13 +688,18 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
     const uint32_t o = s->scenes[q].off;
     for (uint32_t i = 0; i < d.n; ++i) {
       double r = d.radius[i];
-      double m = d.density * 4.0 / 3.0 * pi * r * r * r;
-      double I = 0.4 * m * r * r;
       P[o + i] = make_float4(d.x[i], d.y[i], d.z[i], d.radius[i]);
-      PV[2 * (size_t)(o + i)] = make_float4(d.vx ? d.vx[i] : 0.f, d.vy ? d.vy[i] : 0.f, d.vz ? d.vz[i] : 0.f,
-                                            (float)(1.0 / m));
-      PV[2 * (size_t)(o + i) + 1] = make_float4(d.wx ? d.wx[i] : 0.f, d.wy ? d.wy[i] : 0.f,
-                                                d.wz ? d.wz[i] : 0.f, (float)(1.0 / I));
+      if (!(r > 0.0)) {  // dormant reserve slot: at rest, no mass (1/m = 1/I = 0)
+        PV[2 * (size_t)(o + i)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        PV[2 * (size_t)(o + i) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        double m = d.density * 4.0 / 3.0 * pi * r * r * r;
+        double I = 0.4 * m * r * r;
+        PV[2 * (size_t)(o + i)] = make_float4(d.vx ? d.vx[i] : 0.f, d.vy ? d.vy[i] : 0.f,
+                                              d.vz ? d.vz[i] : 0.f, (float)(1.0 / m));
+        PV[2 * (size_t)(o + i) + 1] = make_float4(d.wx ? d.wx[i] : 0.f, d.wy ? d.wy[i] : 0.f,
+                                                  d.wz ? d.wz[i] : 0.f, (float)(1.0 / I));
+      }
       ids[o + i] = o + i;
       sids[o + i] = q;
     }
@@ -612,7 +707,16 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
       std::memcpy(heights.data() + s->L.geo[q].hf_off, d.hf_heights,
                   sizeof(float) * (d.hf_nx + 1) * (d.hf_ny + 1));
   }
-  if (cudaMemcpyAsync(s->d.pos, P.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
+  std::vector<uint32_t> hf_scene(s->L.nheights, 0u);
+  for (uint32_t q = 0; q < count; ++q)
+    if (descs[q].hf_nx > 0)
+      for (uint32_t k2 = 0; k2 < (descs[q].hf_nx + 1) * (descs[q].hf_ny + 1); ++k2)
+        hf_scene[s->L.geo[q].hf_off + k2] = q;
+  if (cudaMemcpyAsync(s->d.hf_scene, hf_scene.data(), sizeof(uint32_t) * hf_scene.size(), cudaMemcpyHostToDevice,
+                      s->st) ||
+      cudaMemcpyAsync(s->d.hf_top, heights.data(), sizeof(float) * heights.size(), cudaMemcpyHostToDevice, s->st) ||
+      cudaMemsetAsync(s->d.hf_pend, 0, sizeof(float) * heights.size(), s->st) ||
+      cudaMemcpyAsync(s->d.pos, P.data(), sizeof(float4) * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.pv, PV.data(), sizeof(float4) * 2 * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.pid, ids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
       cudaMemcpyAsync(s->d.sid, sids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, s->st) ||
@@ -696,6 +800,7 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool c
   launches += 1;
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[4], s->st, evf));
   launches += tds_launch_finish(d, s->k, s->L.cap, s->st);
+  if (s->any_cutter) launches += tds_launch_cut(d, s->k, s->x.heights, s->L.nheights, s->st);
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[5], s->st, evf));
   std::swap(d.prev_first[0], d.prev_first[1]);
   std::swap(d.prev_cnt[0], d.prev_cnt[1]);
@@ -720,6 +825,7 @@ GraphKey graph_key(const tds_scene *s) {
   g.impact_iters = s->desc.impact_iters;
   g.restitution = s->desc.restitution;
   g.impact_speed = s->desc.impact_speed;
+  g.cutter = s->any_cutter;
   return g;
 }
 
@@ -959,6 +1065,61 @@ tds_status tds_read_particles(tds_scene *s, float *x, float *y, float *z, float 
   return read_particles_impl(s, 0, n, x, y, z, vx, vy, vz, wx, wy, wz);
 }
 
+tds_status tds_set_cutter(tds_scene *s, uint32_t scene, const tds_cutter *c) {
+  if (!s || !c) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (scene >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "scene index out of range");
+  const SceneGeo &G = s->L.geo[scene];
+  if (c->length > 0.f) {
+    if (G.hf_nx <= 0) return fail(TDS_ERR_INVALID_ARG, "a cutter needs the scene's heightfield");
+    const float rmax = s->L.rmax;
+    if (!(c->spawn_radius > 0.f) || c->spawn_radius > rmax || 2.f * c->spawn_radius > G.hf_cell)
+      return fail(TDS_ERR_INVALID_ARG,
+                  "spawn_radius must be in (0, largest radius at creation] and at most half the heightfield cell");
+    if (!(c->bank_density > 0.f) || !(c->phi >= 0.f && c->phi < 1.5707963f))
+      return fail(TDS_ERR_INVALID_ARG, "bank_density > 0 and 0 <= phi < pi/2 required");
+    const double du = std::sqrt((double)c->dir[0] * c->dir[0] + (double)c->dir[1] * c->dir[1] +
+                                (double)c->dir[2] * c->dir[2]);
+    const double dn = std::sqrt((double)c->normal[0] * c->normal[0] + (double)c->normal[1] * c->normal[1] +
+                                (double)c->normal[2] * c->normal[2]);
+    if (!(du > 1e-9) || !(dn > 1e-9) || !std::isfinite(c->length))
+      return fail(TDS_ERR_INVALID_ARG, "edge direction and blade normal must be non-zero");
+  }
+  SceneHost &h = s->scenes[scene];
+  h.cutter = *c;
+  h.has_cutter = c->length > 0.f;
+  compose_boxes(s, scene);
+  s->any_cutter = false;
+  for (const SceneHost &q : s->scenes) s->any_cutter |= q.has_cutter;
+  return TDS_OK;
+}
+
+tds_status tds_read_heightfield(tds_scene *s, uint32_t scene, float *heights, float *pending, uint32_t count) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (scene >= s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "scene index out of range");
+  const SceneGeo &G = s->L.geo[scene];
+  const uint32_t nodes = G.hf_nx > 0 ? (uint32_t)((G.hf_nx + 1) * (G.hf_ny + 1)) : 0u;
+  if (count != nodes) return fail(TDS_ERR_INVALID_ARG, "count differs from the scene's heightfield nodes");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  if (nodes && heights)
+    CUDA_TRY(cudaMemcpyAsync(heights, s->x.heights + G.hf_off, sizeof(float) * nodes, cudaMemcpyDeviceToHost,
+                             s->st));
+  if (nodes && pending)
+    CUDA_TRY(cudaMemcpyAsync(pending, s->d.hf_pend + G.hf_off, sizeof(float) * nodes, cudaMemcpyDeviceToHost,
+                             s->st));
+  return sync_and_check(s);
+}
+
+tds_status tds_read_radii(tds_scene *s, float *r, uint32_t n) {
+  if (!s || !r) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (n != s->L.n) return fail(TDS_ERR_INVALID_ARG, "n differs from the particle count");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  tds_launch_stage(s->d, s->L.n, s->st);
+  CUDA_TRY(cudaMemcpyAsync(r, s->d.stage + (size_t)9 * s->L.n, sizeof(float) * n, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
 tds_status tds_batch_read_particles(tds_scene *s, uint32_t scene, float *x, float *y, float *z, float *vx,
                                     float *vy, float *vz, float *wx, float *wy, float *wz, uint32_t n) {
   if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
@@ -1013,6 +1174,7 @@ tds_status tds_get_stats(tds_scene *s, tds_step_stats *out) {
   out->n_colours = ctr[CTR_NCOL];
   out->colour_rounds = ctr[CTR_ROUNDS];
   out->impacts = s->desc.impact_iters ? ctr[CTR_IMPACTS] : 0;
+  out->spawned = s->any_cutter ? ctr[CTR_SPAWN] : 0;
   out->iterations = ctr[CTR_ITERS];
   out->residual = fs[FS_RESID];
   out->steps = s->steps;

@@ -98,36 +98,18 @@ __device__ __forceinline__ BoxHit box_distance(const BoxF &B, float px, float py
   return r;
 }
 
-__device__ __forceinline__ int cell_axis(float x, float x0, float inv, int n) {
-  float t = floorf((x - x0) * inv);
-  if (!(t >= 0.0f)) return 0;
-  if (t >= (float)(n - 1)) return n - 1;
-  return (int)t;
-}
-
-// Cell of a particle: its scene's block of gnx x gny x gnz cells, then the
-// cell inside it (coordinates clamped to the block, which keeps neighbouring
-// particles in neighbouring cells). z runs fastest, then y, then x: beds are
-// wide and shallow, so slot order walks vertical columns slab by slab and a
-// particle's neighbours lie within about one x-slab of it in slot order (the
-// solver's CTAs then touch only nearby slot ranges).
-__device__ __forceinline__ uint32_t cell_index(const StepConsts &k, const SceneGeo &G, uint32_t sid, float4 p,
-                                               int &cx, int &cy, int &cz) {
-  cx = cell_axis(p.x, G.lo[0], k.cell_inv, k.gnx);
-  cy = cell_axis(p.y, G.lo[1], k.cell_inv, k.gny);
-  cz = cell_axis(p.z, G.lo[2], k.cell_inv, k.gnz);
-  const uint32_t cps = (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
-  return sid * cps + ((uint32_t)cx * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnz + (uint32_t)cz;
-}
-
 // ---------------------------------------------------------------------------
 // broadphase kernels
 // ---------------------------------------------------------------------------
+// Dormant reserve slots (radius 0) go to one trailing cell after all scenes'
+// cells, which no neighbour search visits.
 __global__ void k_cells(DevPtrs d, StepConsts k) {
+  const uint32_t trailing = k.nscenes * (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     int cx, cy, cz;
     const uint32_t sid = d.sid[i];
-    uint32_t c = cell_index(k, k.geo[sid], sid, d.pos[i], cx, cy, cz);
+    const float4 P = d.pos[i];
+    uint32_t c = P.w == 0.0f ? trailing : cell_index(k, k.geo[sid], sid, P, cx, cy, cz);
     d.cell_of[i] = c;
     atomicAdd(d.cell_count + c, 1u);
   }
@@ -173,6 +155,7 @@ __global__ void k_reorder(DevPtrs d, uint32_t n) {
 template <class F>
 __device__ __forceinline__ void for_each_contact(const DevPtrs &d, const StepConsts &k, uint32_t i, F &f) {
   const float4 P = d.pos[i];
+  if (P.w == 0.0f) return;  // dormant reserve slot: no contacts
   const uint32_t me = d.pid[i], sid = d.sid[i];
   const SceneGeo &G = k.geo[sid];
   int cx, cy, cz;
@@ -380,10 +363,11 @@ static inline unsigned grid_for(uint32_t n, unsigned threads, unsigned maxb = 15
 }
 
 int tds_launch_broadphase(const DevPtrs &d, const StepConsts &k, uint32_t ncells, cudaStream_t st) {
-  cudaMemsetAsync(d.cell_count, 0, sizeof(uint32_t) * (ncells + 1), st);
+  // ncells scene cells plus the trailing cell of dormant slots
+  cudaMemsetAsync(d.cell_count, 0, sizeof(uint32_t) * (ncells + 2), st);
   k_cells<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
-  tds_scan_exclusive(d.cell_count, d.cell_start, ncells, d.scan_tmp, st);
-  cudaMemcpyAsync(d.cell_cursor, d.cell_start, sizeof(uint32_t) * ncells, cudaMemcpyDeviceToDevice, st);
+  tds_scan_exclusive(d.cell_count, d.cell_start, ncells + 1, d.scan_tmp, st);
+  cudaMemcpyAsync(d.cell_cursor, d.cell_start, sizeof(uint32_t) * (ncells + 1), cudaMemcpyDeviceToDevice, st);
   k_cell_scatter<<<grid_for(k.n, 256), 256, 0, st>>>(d, k);
   k_cell_sort<<<grid_for(ncells, 256), 256, 0, st>>>(d, ncells);
   k_reorder<<<grid_for(k.n, 256), 256, 0, st>>>(d, k.n);

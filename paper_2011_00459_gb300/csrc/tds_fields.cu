@@ -28,6 +28,7 @@ __global__ void k_cg_scatter(DevPtrs d, uint32_t n, tds_grid g, int kernel, floa
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (d.sid[i] != g.scene) continue;
     const float4 x = d.pos[i];
+    if (x.w == 0.0f) continue;  // dormant reserve slot
     const float4 v = d.pv[2 * (size_t)i];
     const float m = 1.0f / v.w;
     const int ci = voxel_axis(x.x, g.origin[0], g.l0, g.nx);

@@ -43,6 +43,11 @@ struct SceneGeo {
   int cf, ncx, ncy;            // surface columns of the learned warm start (cf 0: none)
   uint32_t col_off;            // first column of the scene in the surface array
   uint32_t pid0;               // first particle id of the scene (ids are global)
+  uint32_t npart;              // its particles (ids pid0 .. pid0 + npart - 1)
+  // active-zone cutter (cut_on 0: none), world frame after the tool pose
+  int cut_on;
+  float e0[3], u[3], ns[3], nf[3];  // edge start, edge direction, blade normal, failure-plane normal
+  float cut_len, rho_b, rs, ms, inv_m, inv_I;
 };
 
 // Per-step constants, passed by value to every kernel.
@@ -64,6 +69,29 @@ struct StepConsts {
   const BoxF *boxes;    // world-frame boxes of all scenes
   const float *heights; // heightfields of all scenes
 };
+
+__device__ __forceinline__ int cell_axis(float x, float x0, float inv, int n) {
+  float t = floorf((x - x0) * inv);
+  if (!(t >= 0.0f)) return 0;
+  if (t >= (float)(n - 1)) return n - 1;
+  return (int)t;
+}
+
+// Cell of a particle: its scene's block of gnx x gny x gnz cells, then the
+// cell inside it (coordinates clamped to the block, which keeps neighbouring
+// particles in neighbouring cells). z runs fastest, then y, then x: beds are
+// wide and shallow, so slot order walks vertical columns slab by slab and a
+// particle's neighbours lie within about one x-slab of it in slot order (the
+// solver's CTAs then touch only nearby slot ranges).
+__device__ __forceinline__ uint32_t cell_index(const StepConsts &k, const SceneGeo &G, uint32_t sid, float4 p,
+                                               int &cx, int &cy, int &cz) {
+  cx = cell_axis(p.x, G.lo[0], k.cell_inv, k.gnx);
+  cy = cell_axis(p.y, G.lo[1], k.cell_inv, k.gny);
+  cz = cell_axis(p.z, G.lo[2], k.cell_inv, k.gnz);
+  const uint32_t cps = (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
+  return sid * cps + ((uint32_t)cx * (uint32_t)k.gny + (uint32_t)cy) * (uint32_t)k.gnz + (uint32_t)cz;
+}
+
 
 // Device pointers of one scene (passed by value).
 struct DevPtrs {
@@ -126,6 +154,12 @@ struct DevPtrs {
   float *targ;                // 3 targets per contact (recording)
   uint8_t *c_flag;            // 1 if the contact's key existed in the previous step
   uint32_t *new_idx;          // learned warm start without recording: the contacts it starts
+  // active-zone cut: per heightfield node (all scenes) pending mass, highest
+  // height so far, scene, particle count and rank; per particle id the
+  // dormant flag/rank and slot
+  float *hf_pend, *hf_top;
+  uint32_t *hf_scene, *hf_cnt, *hf_rank;
+  uint32_t *dorm_rank, *dorm_list, *slot_of_pid;
   float4 *p_il;               // impact stage, colour order: impulses (n, t1, t2, r.x)
   float4 *p_il2;              //   (r.y, r.z, G_n v* before the stage, normal target)
 };
@@ -134,7 +168,7 @@ struct DevPtrs {
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_IMPACTS = 13,
-       CTR_NEW = 14, CTR_COUNT = 16 };
+       CTR_NEW = 14, CTR_SPAWN = 15, CTR_COUNT = 16 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
 // ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
 // static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.

@@ -375,6 +375,7 @@ __global__ void k_columns(DevPtrs d, StepConsts k, int *surf) {
     const SceneGeo &G = k.geo[d.sid[i]];
     if (G.cf <= 0) continue;
     const float4 P = d.pos[i];
+    if (P.w == 0.0f) continue;  // dormant reserve slot
     atomicMax(surf + column_of(G, P.x, P.y), ordered(__fadd_rn(P.z, P.w)));
   }
 }

@@ -22,6 +22,7 @@ __device__ __forceinline__ bool is_dyn(uint32_t b) { return (b & TDS_STATIC) == 
 __global__ void k_predict(DevPtrs d, StepConsts k) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     float4 v = d.pv[2 * i];
+    if (v.w == 0.0f) continue;  // dormant reserve slot (1/m = 0): no gravity
     v.x += k.dt * k.g[0];
     v.y += k.dt * k.g[1];
     v.z += k.dt * k.g[2];
@@ -837,7 +838,7 @@ __global__ void k_stage(DevPtrs d, uint32_t n) {
     d.stage[2 * (size_t)n + id] = p.z; d.stage[3 * (size_t)n + id] = v.x;
     d.stage[4 * (size_t)n + id] = v.y; d.stage[5 * (size_t)n + id] = v.z;
     d.stage[6 * (size_t)n + id] = w.x; d.stage[7 * (size_t)n + id] = w.y;
-    d.stage[8 * (size_t)n + id] = w.z;
+    d.stage[8 * (size_t)n + id] = w.z; d.stage[9 * (size_t)n + id] = p.w;
   }
 }
 

@@ -33,7 +33,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
             "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid",
-            "tds_set_impact"]
+            "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 
@@ -77,7 +77,8 @@ class StepStats(ctypes.Structure):
                 ("timed_steps", ctypes.c_uint32), ("phase_ms", ctypes.c_float * 5),
                 ("sweep_contacts_pp", ctypes.c_uint64), ("sweep_contacts_static", ctypes.c_uint64),
                 ("sum_contacts", ctypes.c_uint64), ("solved_steps", ctypes.c_uint64),
-                ("colour_rounds", ctypes.c_uint32), ("impacts", ctypes.c_uint32)]
+                ("colour_rounds", ctypes.c_uint32), ("impacts", ctypes.c_uint32),
+                ("spawned", ctypes.c_uint32)]
 
 PHASES = ("broadphase", "narrowphase", "colouring", "pgs", "finish")
 
@@ -124,6 +125,12 @@ def advect_fluid(grid: Grid, u, rho, dt: float, source=None, out=None, stream=No
     return out
 
 
+class Cutter(ctypes.Structure):
+    _fields_ = [("edge", ctypes.c_float * 3), ("dir", ctypes.c_float * 3), ("length", ctypes.c_float),
+                ("normal", ctypes.c_float * 3), ("phi", ctypes.c_float), ("bank_density", ctypes.c_float),
+                ("spawn_radius", ctypes.c_float)]
+
+
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pgs_blocks", ctypes.c_int32), ("pgs_sync", ctypes.c_int32),
                 ("colour_blocks", ctypes.c_int32), ("max_pgs_blocks", ctypes.c_int32),
@@ -161,6 +168,9 @@ def lib() -> ctypes.CDLL:
         L.tds_set_recording.argtypes = [vp, ctypes.c_int32]
         L.tds_set_warm_start.argtypes = [vp, ctypes.c_int32]
         L.tds_set_impact.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
+        L.tds_set_cutter.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(Cutter)]
+        L.tds_read_heightfield.argtypes = [vp, ctypes.c_uint32, vp, vp, ctypes.c_uint32]
+        L.tds_read_radii.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_read_training_samples.argtypes = [vp, vp, vp, vp, ctypes.c_uint32,
                                                 ctypes.POINTER(ctypes.c_uint32)]
         L.tds_mlp_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
@@ -389,6 +399,35 @@ class Scene:
     def set_impact(self, restitution: float, impact_speed: float, iters: int):
         """Impact stage settings (iters 0 disables it)."""
         _check(lib().tds_set_impact(self.h, float(restitution), float(impact_speed), int(iters)))
+
+    def set_cutter(self, cutter: dict | None, scene: int = 0):
+        """Active-zone cutter on the scene's tool (tool-frame edge point,
+        edge direction, length, blade normal, phi [rad], bank density, spawn
+        radius); None removes it."""
+        c = Cutter()
+        if cutter is not None:
+            for k in ("edge", "dir", "normal"):
+                for i in range(3):
+                    getattr(c, k)[i] = float(cutter[k][i])
+            c.length = float(cutter["length"])
+            c.phi, c.bank_density = float(cutter["phi"]), float(cutter["bank_density"])
+            c.spawn_radius = float(cutter["spawn_radius"])
+        _check(lib().tds_set_cutter(self.h, int(scene), ctypes.byref(c)))
+
+    def read_heightfield(self, scene: int = 0, shape=None):
+        """Current heights and pending mass per node, (ny+1, nx+1) float32."""
+        d = self._descs[scene]
+        ny, nx = int(d.hf_ny) + 1, int(d.hf_nx) + 1
+        h = np.empty(nx * ny, np.float32)
+        p = np.empty(nx * ny, np.float32)
+        _check(lib().tds_read_heightfield(self.h, int(scene), ctypes.c_void_p(h.ctypes.data),
+                                          ctypes.c_void_p(p.ctypes.data), nx * ny))
+        return h.reshape(ny, nx), p.reshape(ny, nx)
+
+    def read_radii(self) -> np.ndarray:
+        r = np.empty(self.n, np.float32)
+        _check(lib().tds_read_radii(self.h, ctypes.c_void_p(r.ctypes.data), self.n))
+        return r
 
     def set_warm_start(self, mode: int):
         _check(lib().tds_set_warm_start(self.h, int(mode)))

@@ -1,7 +1,8 @@
 """Pins of the active-zone oracle (Eq. failure_plane and the terrain-to-particle
 conversion): the failure angle reduces to Rankine's for an upright blade, the
 volume cut from a flat bed is the wedge's closed-form prism, mass is conserved,
-new particles sit in their columns without overlaps, an existing particle blocks
+new particles sit in their columns without overlaps and clear the terrain
+around their node (FP64 geometry), an existing particle blocks
 the positions it overlaps, dormant ids are used in order, and nothing is cut
 above the surface or behind the blade."""
 import math
@@ -80,6 +81,51 @@ def test_mass_is_conserved_and_particles_fit_their_columns():
     from scipy.spatial import cKDTree
 
     assert len(cKDTree(pos.astype(np.float64)).query_pairs(2 * rs - 1e-6)) == 0  # no overlaps
+
+
+def terrain_clearance(hf, h, i, j, z):
+    """FP64 distance of the point z above node (i, j) from the nearest plane
+    of the triangles having the node as a corner (cells split along the
+    (a+1, b)-(a, b+1) diagonal)."""
+    c = float(hf["cell"])
+    corner = lambda a, b: np.array([a * c, b * c, float(h[b, a])])
+    p = np.array([i * c, j * c, z])
+    best = np.inf
+    for a in (i - 1, i):
+        for b in (j - 1, j):
+            if not (0 <= a < hf["nx"] and 0 <= b < hf["ny"]):
+                continue
+            for tri in ([(a, b), (a + 1, b), (a, b + 1)], [(a + 1, b + 1), (a, b + 1), (a + 1, b)]):
+                if (i, j) not in tri:
+                    continue
+                A, B, C = (corner(*t) for t in tri)
+                n = np.cross(B - A, C - A)
+                n /= np.linalg.norm(n) * np.sign(n[2])
+                best = min(best, float(n @ (p - A)))
+    return best
+
+
+def test_new_particles_clear_the_terrain_around_their_node():
+    hf, W, x, r = conversion_case()
+    h, pend, ids, pos, lib = run(hf, W, x, r)
+    rs = float(W["rs"])
+    cell = float(hf["cell"])
+    first = {}
+    for p in pos.astype(np.float64):
+        i, j = int(round(p[0] / cell)), int(round(p[1] / cell))
+        assert terrain_clearance(hf, h, i, j, p[2]) >= rs - 1e-6
+        first[(i, j)] = min(first.get((i, j), np.inf), p[2])
+    # nothing else in the way: each column starts at the lowest position
+    # z_f + r_s (1 + 2q) that clears the terrain
+    steep = 0
+    for (i, j), z in first.items():
+        zf = float(h[j, i])
+        q0 = next(q for q in range(64) if terrain_clearance(hf, h, i, j, zf + rs * (1 + 2 * q)) >= rs + 1e-6)
+        assert z == pytest.approx(zf + rs * (1 + 2 * q0), abs=1e-6) or (
+            z == pytest.approx(zf + rs * (1 + 2 * (q0 - 1)), abs=1e-6)
+            and terrain_clearance(hf, h, i, j, z) == pytest.approx(rs, abs=1e-6))
+        steep += q0 > 0
+    assert steep > 0  # columns beside uncut terrain start higher up
 
 
 def test_an_existing_particle_blocks_what_it_overlaps():
