@@ -345,9 +345,11 @@ tds_status tds_advect_fluid(const tds_grid *grid, const float *u, const float *r
  * the cell area becomes the node's pending mass. A node cut this step then
  * places particles of radius spawn_radius at rest in its liberated column
  * (from its height up to the highest it has been), j-th at
- * height + spawn_radius (1 + 2j), first fit: a position is taken when no
- * active particle overlaps it (FP32 test) and the pending mass pays for a
- * particle (particle density); nodes in index order, each particle taking the
+ * height + spawn_radius (1 + 2j), first fit: a position is taken when it
+ * lies at least spawn_radius from the planes of the heightfield triangles
+ * around the node (heights after the step's cut), no active particle overlaps
+ * it (FP32 test) and the pending mass pays for a particle (particle density);
+ * nodes in index order, each particle taking the
  * scene's next dormant slot (radius 0, in increasing id order). Mass that finds
  * no place or slot stays pending. Not modelled: fluidized mass, the reverse
  * conversion (deposition, gap filling). All in FP32 on the device, after the
