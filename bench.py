@@ -702,11 +702,12 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
     return n * k / el, desc, k
 
 
-def learned_form(args, launch_cfg, stream) -> dict:
-    """The learned warm start on the headline's bed: an identical preparation
-    (same settle, launch shapes, approach and warm-up with the previous-step
-    warm start), then the same timed steps with the network trained on plain
-    solves of the small and bulldozing beds (weights shipped with the package)."""
+def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dict:
+    """The learned warm start on the workload of ``args``: an identical
+    preparation (same settle, launch shapes, approach and warm-up with the
+    previous-step warm start), then the same timed steps with the network
+    trained on plain solves of the small and bulldozing beds (weights shipped
+    with the package)."""
     import torch
 
     from paper_2011_00459_gb300 import learned as LR
@@ -734,21 +735,26 @@ def learned_form(args, launch_cfg, stream) -> dict:
     return {"warm_start": "learned (10-64-64-3 BF16 network)", "value": sim.n * args.steps / (ms * 1e-3),
             "unit": UNIT, "ms_per_step": ms / args.steps,
             "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
-            "final_residual": st["residual"], "steps": "the same steps as the headline (identical preparation)"}
+            "final_residual": st["residual"], "steps": f"the same steps as {same_as} (identical preparation)"}
 
 
-def batched_form(args, rank: int, world: int, local_rank: int) -> dict:
-    """The batched workload (256 beds in one graph-replayed batch) at the same
-    residual, timed like the headline."""
+def batched_args(args):
     import copy
 
     a = copy.copy(args)
     a.workload, a.no_e2e, a.roofline_sweeps, a.no_cpu_baseline = "batched", True, 0, True
+    return a
+
+
+def batched_form(args, rank: int, world: int, local_rank: int) -> tuple:
+    """The batched workload (256 beds in one graph-replayed batch) at the same
+    residual, timed like the headline; also returns its launch shape."""
+    a = batched_args(args)
     work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(a, rank, world, local_rank)
-    return {"workload": describe(work, a)["workload"], "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT,
-            "ms_per_step": ms / a.steps,
-            "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
-            "final_residual": st["residual"], "gpu_launches": int(launches)}
+    return ({"workload": describe(work, a)["workload"], "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT,
+             "ms_per_step": ms / a.steps, "warm_start": "previous step",
+             "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
+             "final_residual": st["residual"], "gpu_launches": int(launches)}, launch_cfg)
 
 
 def sample_scene(work) -> dict:
@@ -845,9 +851,12 @@ def main():
             result["forms"]["learned"] = {"error": repr(exc)}
         if args.workload == "large":
             try:
-                result["forms"]["batched"] = batched_form(args, rank, world, local_rank)
+                result["forms"]["batched"], bcfg = batched_form(args, rank, world, local_rank)
+                result["forms"]["batched_learned"] = learned_form(batched_args(args), bcfg, torch.cuda.Stream(),
+                                                                  "the batched form")
             except Exception as exc:
-                result["forms"]["batched"] = {"error": repr(exc)}
+                result["forms"].setdefault("batched", {"error": repr(exc)})
+                result["forms"].setdefault("batched_learned", {"error": repr(exc)})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
 
