@@ -757,6 +757,26 @@ def batched_form(args, rank: int, world: int, local_rank: int) -> tuple:
              "final_residual": st["residual"], "gpu_launches": int(launches)}, launch_cfg)
 
 
+def unbatched_form(args, rank: int, world: int, local_rank: int, steps: int = 3) -> dict:
+    """The batch's beds stepped one scene at a time (each bed its own launch
+    sequence every step) against the batch itself, on identical preparations
+    and the same steps; each form stops at its own residual test (the batch:
+    one norm over all beds; a separate bed: its own)."""
+    out = {}
+    for unb in (False, True):
+        a = batched_args(args)
+        a.steps, a.unbatched = min(args.steps, steps), unb
+        work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(a, rank, world, local_rank)
+        out["unbatched" if unb else "batched"] = {
+            "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / a.steps,
+            "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
+            "gpu_launches": int(launches)}
+    out["steps"] = min(args.steps, steps)
+    out["scenes"] = len(work)
+    out["speedup"] = out["batched"]["value"] / out["unbatched"]["value"]
+    return out
+
+
 def sample_scene(work) -> dict:
     """The scene the oracle samples: the bed itself, or the batch's bed of
     median size."""
@@ -857,6 +877,10 @@ def main():
             except Exception as exc:
                 result["forms"].setdefault("batched", {"error": repr(exc)})
                 result["forms"].setdefault("batched_learned", {"error": repr(exc)})
+            try:
+                result["forms"]["batched_vs_unbatched"] = unbatched_form(args, rank, world, local_rank)
+            except Exception as exc:
+                result["forms"]["batched_vs_unbatched"] = {"error": repr(exc)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
 

@@ -64,19 +64,29 @@ def store_cache(key: str, entry: dict, path: str | None = None) -> None:
     os.replace(tmp, path)
 
 
+SYNC_MODES = (1, 0)  # neighbour synchronisation, grid barrier
+
+
 def candidates(cfg: dict, sms: int) -> list:
-    """Launch shapes to time, the library's defaults first."""
-    maxp, maxc = cfg["max_pgs_blocks"], cfg["max_colour_blocks"]
+    """Solver shapes to time (sync mode x solver CTAs, the colouring CTAs
+    kept), the library's defaults first."""
+    maxp = cfg["max_pgs_blocks"]
     pgs = sorted({min(maxp, cfg["pgs_blocks"]), min(maxp, max(1, (3 * cfg["pgs_blocks"]) // 4))}, reverse=True)
-    col = sorted({min(maxc, c) for c in (cfg["colour_blocks"], sms, 2 * sms, maxc) if c >= 1}, reverse=True)
     out = [dict(pgs_blocks=cfg["pgs_blocks"], pgs_sync=cfg["pgs_sync"], colour_blocks=cfg["colour_blocks"])]
-    for sync in (1, 0):
+    for sync in SYNC_MODES:
         for p in pgs:
-            for c in col:
-                shape = dict(pgs_blocks=p, pgs_sync=sync, colour_blocks=c)
-                if shape not in out:
-                    out.append(shape)
+            shape = dict(pgs_blocks=p, pgs_sync=sync, colour_blocks=cfg["colour_blocks"])
+            if shape not in out:
+                out.append(shape)
     return out
+
+
+def colour_candidates(cfg: dict, best: dict, sms: int) -> list:
+    """Colouring CTAs to time on the chosen solver shape (the colouring and
+    the solver are separate kernels, so the two choices do not interact)."""
+    maxc = cfg["max_colour_blocks"]
+    col = sorted({min(maxc, c) for c in (cfg["colour_blocks"], sms, 2 * sms, maxc) if c >= 1}, reverse=True)
+    return [dict(best, colour_blocks=c) for c in col if c != best["colour_blocks"]]
 
 
 def time_steps(sim, steps: int) -> float:
@@ -119,14 +129,20 @@ def tune(sim, steps: int = 3, sweeps: int = 50, use_cache: bool = True, path: st
     saved = g.solver
     g.set_solver(sweeps, 0.0, 10)
     results = []
-    try:
-        for shape in candidates(cfg, props.multi_processor_count):
+
+    def timed(shapes):
+        for shape in shapes:
             g.set_launch_config(**shape)
             sim.advance()  # first step of a shape (graph capture, if any) is not timed
             ms = time_steps(sim, steps)
             results.append((ms, shape))
             if log:
                 log(f"autotune: {shape} {ms:.3f} ms/step")
+        return min(results, key=lambda r: r[0])[1]
+
+    sms = props.multi_processor_count
+    try:
+        timed(colour_candidates(cfg, timed(candidates(cfg, sms)), sms))
     finally:
         g.set_solver(*saved)
     ms, best = min(results, key=lambda r: r[0])

@@ -40,8 +40,13 @@ def test_candidates_start_with_the_defaults_and_stay_in_limits():
     assert c[0] == {"pgs_blocks": 152, "pgs_sync": 1, "colour_blocks": 608}
     assert len(c) == len({tuple(sorted(x.items())) for x in c})
     for x in c:
-        assert 1 <= x["pgs_blocks"] <= 152 and 1 <= x["colour_blocks"] <= 1216 and x["pgs_sync"] in (0, 1)
+        assert 1 <= x["pgs_blocks"] <= 152 and x["colour_blocks"] == 608 and x["pgs_sync"] in (0, 1)
     assert {x["pgs_sync"] for x in c} == {0, 1}
+    best = c[-1]
+    cc = A.colour_candidates(cfg, best, 152)
+    assert cc and all(dict(x, colour_blocks=best["colour_blocks"]) == best for x in cc)
+    assert all(1 <= x["colour_blocks"] <= 1216 and x["colour_blocks"] != best["colour_blocks"] for x in cc)
+    assert len(c) + len(cc) <= 12  # the tuner times them inside a settle reserve of 80 steps
     small = A.candidates({"pgs_blocks": 3, "pgs_sync": 0, "colour_blocks": 608, "max_pgs_blocks": 152,
                           "max_colour_blocks": 1216}, 152)
     assert min(x["pgs_blocks"] for x in small) >= 1
