@@ -33,8 +33,15 @@
  *    or the default stream when none is given). tds_step returns without
  *    waiting for the GPU; the read calls and tds_synchronize wait.
  *  - Errors detected on the device (capacity overflow, non-finite state,
- *    a grid barrier that timed out) are latched in the scene and returned by
- *    the next waiting call; the scene is then unusable until destroyed.
+ *    a grid barrier that timed out) are latched by the step that meets them
+ *    and returned by the next waiting call (a read, tds_synchronize,
+ *    tds_get_stats). That step and the steps queued after it change nothing,
+ *    and the waiting call puts the scene back at the state before the failing
+ *    step: particles, warm-start memory and heightfield as they were, the
+ *    step count reduced accordingly (tds_get_stats). The scene is usable
+ *    again; the call that reports the error leaves its output buffers
+ *    unspecified. An error that no step raised leaves the scene unusable
+ *    (TDS_ERR_STATE) until destroyed.
  *  - Not thread-safe per scene; distinct scenes may be used concurrently.
  */
 #ifndef TDS_H
@@ -54,7 +61,7 @@ typedef enum {
   TDS_ERR_CAPACITY = -4,        /* more contacts or colours than the scene's capacity */
   TDS_ERR_NONFINITE = -5,       /* a particle velocity or position became NaN/Inf */
   TDS_ERR_BARRIER_TIMEOUT = -6, /* a grid-wide barrier waited longer than its limit */
-  TDS_ERR_STATE = -7            /* the scene already holds an error */
+  TDS_ERR_STATE = -7            /* the scene holds an error no step raised, or a call out of order */
 } tds_status;
 
 typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1, TDS_WARM_LEARNED = 2 } tds_warm_start;
@@ -182,7 +189,8 @@ tds_status tds_set_warm_start(tds_scene *s, int32_t mode);
 /* Advance nsteps time steps (asynchronous). */
 tds_status tds_step(tds_scene *s, uint32_t nsteps);
 
-/* Wait for the scene's stream; returns a latched device error, if any. */
+/* Wait for the scene's stream; returns a latched device error, if any (the
+ * scene is then back at the state before the failing step). */
 tds_status tds_synchronize(tds_scene *s);
 
 /* Copy the particle state to host arrays of n floats (any pointer may be

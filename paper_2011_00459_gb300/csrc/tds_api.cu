@@ -569,13 +569,50 @@ const char *dev_err_text(int32_t e) {
   }
 }
 
+// The buffers one step swaps: particle state (sorted copy / previous order)
+// and warm-start memory (read / written this step).
+void swap_state(DevPtrs &d) {
+  std::swap(d.pos, d.pos2);
+  std::swap(d.pv, d.pv2);
+  std::swap(d.pid, d.pid2);
+  std::swap(d.sid, d.sid2);
+  std::swap(d.prev_first[0], d.prev_first[1]);
+  std::swap(d.prev_cnt[0], d.prev_cnt[1]);
+  std::swap(d.prev_other[0], d.prev_other[1]);
+  std::swap(d.prev_l0[0], d.prev_l0[1]);
+  std::swap(d.prev_l1[0], d.prev_l1[1]);
+}
+
+// Waits for the scene's stream and reports a latched device error. A failing
+// step leaves the scene as it was before that step: the error was latched in
+// the last step that started clean (CTR_CLEAN counts them), no kernel wrote
+// state after it, and that step's input still sits in the buffers the step
+// swapped away from. Restoring their parity (and clearing the error) makes
+// the scene usable again; the call returns the error.
 tds_status sync_and_check(tds_scene *s) {
   CUDA_TRY(cudaStreamSynchronize(s->st));
   int32_t e = 0;
   CUDA_TRY(cudaMemcpy(&e, s->d.err, sizeof(e), cudaMemcpyDeviceToHost));
   if (e != 0) {
-    s->latched = (tds_status)e;
-    return fail((tds_status)e, dev_err_text(e));
+    uint32_t clean = 0;
+    CUDA_TRY(cudaMemcpy(&clean, s->d.ctr + CTR_CLEAN, sizeof(clean), cudaMemcpyDeviceToHost));
+    if (clean == 0 || clean > s->steps) {  // not raised by a step: keep it
+      s->latched = (tds_status)e;
+      return fail((tds_status)e, dev_err_text(e));
+    }
+    const uint64_t keep = clean - 1u;  // steps that completed
+    if ((s->steps - keep) & 1u) {
+      swap_state(s->d);
+      s->parity ^= 1u;
+    }
+    s->steps = keep;
+    s->have_prev = keep > 0;
+    const int32_t zero = 0;
+    const uint32_t k32 = (uint32_t)keep;
+    CUDA_TRY(cudaMemcpy(s->d.err, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(s->d.ctr + CTR_CLEAN, &k32, sizeof(k32), cudaMemcpyHostToDevice));
+    return fail((tds_status)e, std::string(dev_err_text(e)) + " in step " + std::to_string(clean) +
+                                   "; the scene is back at the state before that step");
   }
   return TDS_OK;
 }
@@ -884,16 +921,8 @@ tds_status step_graph(tds_scene *s, cudaEvent_t *E) {
     for (int q = 0; q < 6; ++q) CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(g.exec, g.ev_node[q], E[q]));
   CUDA_TRY(cudaGraphLaunch(g.exec, s->st));
   s->launches += g.launches;
-  DevPtrs &d = s->d;  // the same swaps as the captured step
-  std::swap(d.pos, d.pos2);
-  std::swap(d.pv, d.pv2);
-  std::swap(d.pid, d.pid2);
-  std::swap(d.sid, d.sid2);
-  std::swap(d.prev_first[0], d.prev_first[1]);
-  std::swap(d.prev_cnt[0], d.prev_cnt[1]);
-  std::swap(d.prev_other[0], d.prev_other[1]);
-  std::swap(d.prev_l0[0], d.prev_l0[1]);
-  std::swap(d.prev_l1[0], d.prev_l1[1]);
+  DevPtrs &d = s->d;
+  swap_state(d);  // the same swaps as the captured step
   d.targ = s->recording ? s->x.targ : nullptr;
   return TDS_OK;
 }

@@ -104,6 +104,8 @@ __device__ __forceinline__ BoxHit box_distance(const BoxF &B, float px, float py
 // Dormant reserve slots (radius 0) go to one trailing cell after all scenes'
 // cells, which no neighbour search visits.
 __global__ void k_cells(DevPtrs d, StepConsts k) {
+  // steps that start with no error latched (the host finds a failing step by it)
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !step_failed(d)) atomicAdd(d.ctr + CTR_CLEAN, 1u);
   const uint32_t trailing = k.nscenes * (uint32_t)k.gnx * (uint32_t)k.gny * (uint32_t)k.gnz;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     int cx, cy, cz;
@@ -138,6 +140,7 @@ __global__ void k_cell_sort(DevPtrs d, uint32_t ncells) {
 }
 
 __global__ void k_reorder(DevPtrs d, uint32_t n) {
+  if (step_failed(d)) return;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     uint32_t i = d.perm[j];
     d.pos2[j] = d.pos[i];

@@ -117,6 +117,7 @@ __device__ uint32_t place(const DevPtrs &d, const StepConsts &k, const SceneGeo 
 // The cut: nodes in the wedge lowered onto the failure plane, the removed
 // mass added to their pending mass; hf_cnt marks the nodes cut this step.
 __global__ void k_cut(DevPtrs d, StepConsts k, float *heights, uint32_t nh) {
+  if (step_failed(d)) return;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nh; q += gridDim.x * blockDim.x) {
     const uint32_t scene = d.hf_scene[q];
     const SceneGeo &G = k.geo[scene];
@@ -140,6 +141,7 @@ __global__ void k_cut(DevPtrs d, StepConsts k, float *heights, uint32_t nh) {
 // Particles each node cut this step can place (all cuts done: the terrain
 // test sees the final heights).
 __global__ void k_cut_count(DevPtrs d, StepConsts k, const float *heights, uint32_t nh) {
+  if (step_failed(d)) return;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nh; q += gridDim.x * blockDim.x) {
     if (!d.hf_cnt[q]) continue;
     const uint32_t scene = d.hf_scene[q];
@@ -164,6 +166,7 @@ __global__ void k_dorm_list(DevPtrs d, uint32_t n) {
 }
 
 __global__ void k_cut_write(DevPtrs d, StepConsts k, const float *heights, uint32_t nh) {
+  if (step_failed(d)) return;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < nh; q += gridDim.x * blockDim.x) {
     const uint32_t cnt = d.hf_cnt[q];
     if (cnt == 0) continue;

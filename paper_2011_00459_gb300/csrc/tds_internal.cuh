@@ -168,7 +168,7 @@ struct DevPtrs {
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_IMPACTS = 13,
-       CTR_NEW = 14, CTR_SPAWN = 15, CTR_COUNT = 16 };
+       CTR_NEW = 14, CTR_SPAWN = 15, CTR_CLEAN = 16, CTR_COUNT = 17 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
 // ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
 // static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.
@@ -219,6 +219,13 @@ __device__ __forceinline__ unsigned long long priority(unsigned long long key) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
+
+// A step that latched an error changes no state from there on, and the
+// steps queued after it do nothing: every kernel that writes particle state,
+// warm-start memory, the heightfield or the tool force returns at once while
+// an error is latched. The state buffers of the failing step's start then
+// stay intact for the host to restore.
+__device__ __forceinline__ bool step_failed(const DevPtrs &d) { return *(volatile const int32_t *)d.err != 0; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

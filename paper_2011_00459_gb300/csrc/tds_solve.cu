@@ -20,6 +20,7 @@ namespace {
 __device__ __forceinline__ bool is_dyn(uint32_t b) { return (b & TDS_STATIC) == 0u; }
 
 __global__ void k_predict(DevPtrs d, StepConsts k) {
+  if (step_failed(d)) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     float4 v = d.pv[2 * i];
     if (v.w == 0.0f) continue;  // dormant reserve slot (1/m = 0): no gravity
@@ -390,6 +391,7 @@ __device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
 // kPerThread contacts (through L2) before solving any of them (contacts of
 // one colour touch disjoint particles).
 __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
+  if (step_failed(d)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long full[kStages];
   __shared__ uint32_t s_lo[2 * TDS_MAX_COLOURS], s_hi[2 * TDS_MAX_COLOURS], s_nw[TDS_MAX_COLOURS];
@@ -669,6 +671,7 @@ struct ImpactArgs {
 };
 
 __global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
+  if (step_failed(d)) return;
   __shared__ uint32_t s_count;
   const uint32_t ncol = min(d.ctr[CTR_NCOL], (uint32_t)TDS_MAX_COLOURS);
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -729,6 +732,7 @@ __global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
 // impulses with the tangent in world coordinates); per particle id the range
 // of its owned contacts.
 __global__ void k_writeback(DevPtrs d) {
+  if (step_failed(d)) return;
   const uint32_t np = d.ctr[CTR_PADDED];
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     uint32_t c = d.order[p];
@@ -752,6 +756,7 @@ __global__ void k_writeback(DevPtrs d) {
 }
 
 __global__ void k_prev_ranges(DevPtrs d, uint32_t n, uint32_t cap) {
+  if (step_failed(d)) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t s = d.cstart[i], e = d.cstart[i + 1];
     if (s > cap) s = cap;
@@ -763,6 +768,7 @@ __global__ void k_prev_ranges(DevPtrs d, uint32_t n, uint32_t cap) {
 }
 
 __global__ void k_integrate(DevPtrs d, StepConsts k) {
+  if (step_failed(d)) return;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
     float4 p = d.pos[i], v = d.pv[2 * i], w = d.pv[2 * i + 1];
     p.x += k.dt * v.x;
@@ -781,6 +787,7 @@ __global__ void k_integrate(DevPtrs d, StepConsts k) {
 // result is reproducible.
 constexpr int kToolBlocks = 128;
 __global__ void k_tool_partial(DevPtrs d, StepConsts k) {
+  if (step_failed(d)) return;
   __shared__ double sh[8];
   const uint32_t np = d.ctr[CTR_PADDED];
   double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -815,6 +822,7 @@ __global__ void k_tool_partial(DevPtrs d, StepConsts k) {
 }
 
 __global__ void k_tool_final(DevPtrs d, uint32_t nscenes) {
+  if (step_failed(d)) return;
   if (nscenes == 1) {
     if (threadIdx.x < 6) {
       double t = 0.0;
