@@ -49,6 +49,19 @@ __device__ __forceinline__ bool higher(const DevPtrs &d, uint2 e, unsigned long 
 
 constexpr int kBatch = 8;
 
+// A slot in a frontier list for each calling lane: one atomic per group of
+// converged lanes instead of one per lane (the frontier counter is a single
+// address that every released contact would otherwise hit).
+__device__ __forceinline__ uint32_t frontier_slot(uint32_t *counter) {
+  const unsigned mask = __activemask();
+  const unsigned lane = threadIdx.x & 31u;
+  const int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if ((int)lane == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
+}
+
 // wait[c] = number of neighbours of higher priority; sources start round 0.
 __global__ void k_colour_init(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
@@ -71,7 +84,7 @@ __global__ void k_colour_init(DevPtrs d) {
     d.wait[c] = w;
     d.colour[c] = TDS_NO_COLOUR;
     if (w == 0) {
-      uint32_t q = atomicAdd(d.ctr + CTR_FCOUNT, 1u);
+      const uint32_t q = frontier_slot(d.ctr + CTR_FCOUNT);
       if (q < nc) d.frontier0[q] = c;
     }
   }
@@ -125,8 +138,8 @@ __global__ void k_colour_rounds(DevPtrs d) {
       else { col = TDS_MAX_COLOURS - 1; latch_error(d.err, DEV_ERR_CAPACITY); }
       __stcg(d.colour + c, (uint8_t)col);
       atomicMax(&s_maxcol, col + 1);
-      __threadfence();
-      // release the lower-priority neighbours
+      // release the lower-priority neighbours (they read this colour in a
+      // later round, after the grid barrier has published it)
       for (int k = 0; k < 2; ++k) {
         if (!is_dyn(ends[k])) continue;
         const uint32_t s = d.inc_start[ends[k]], e = d.inc_start[ends[k] + 1];
@@ -141,7 +154,7 @@ __global__ void k_colour_rounds(DevPtrs d) {
 #pragma unroll
           for (int q = 0; q < kBatch; ++q)
             if (old[q] == 1) {
-              uint32_t slot = atomicAdd(push, 1u);
+              const uint32_t slot = frontier_slot(push);
               if (slot < nc) nxt[slot] = ent[q].x;
             }
         }
