@@ -415,6 +415,7 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   size_t nd = 2 * (size_t)pgs_blocks;
   if (nd < 6 * 128) nd = 6 * 128;
   d.dpart = c.take<double>(nd);
+  d.dres = c.take<double>(2 * (((size_t)cap + TDS_ORDER_PAD + 255) / 256 + 1));
   d.bar = c.take<uint32_t>(2);
   d.prog = c.take<uint32_t>(kProgStride * (size_t)pgs_blocks);
   d.rng = c.take<uint32_t>(2 * (size_t)pgs_blocks);

@@ -140,6 +140,7 @@ struct DevPtrs {
   unsigned long long *acc;    // see ACC_* below (sums over steps, reset by the host)
   float *fscal;               // see FS_* below
   double *dpart;              // per-block partial sums
+  double *dres;               // solver residual: per chunk of the colour order (numerator, denominator)
   uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
   uint32_t *prog;             // solver neighbour sync: last colour phase published per CTA,
                               // one flag per kProgStride words (own 128-byte line)

@@ -196,11 +196,13 @@ struct SolveArgs {
 // ---------------------------------------------------------------------------
 // Staging of the contact rows and impulses with bulk copies (TMA)
 // ---------------------------------------------------------------------------
-constexpr int kPgsThreads = 512;
-constexpr int kPerThread = 3;                        // contacts per thread per wave
+constexpr int kPgsThreads = 768;
+constexpr int kPerThread = 1;                        // contacts per thread per wave
 constexpr int kWave = kPgsThreads * kPerThread;      // contacts per wave
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
+constexpr uint32_t kResChunk = 256;                  // residual: contacts per chunk of the colour order
+constexpr uint32_t kResSum = 512;                    // residual: threads adding up the chunks
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
 //              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
 constexpr size_t kRowBytes = 72;
@@ -395,7 +397,8 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long full[kStages];
   __shared__ uint32_t s_lo[2 * TDS_MAX_COLOURS], s_hi[2 * TDS_MAX_COLOURS], s_nw[TDS_MAX_COLOURS];
-  __shared__ double sh[kPgsThreads / 32];
+  __shared__ double s_rn[kResSum], s_rd[kResSum];
+  static_assert(kPgsThreads >= (int)kResSum, "the residual sum needs kResSum threads");
   __shared__ uint32_t s_mn[kPgsThreads / 32], s_mx[kPgsThreads / 32];
   __shared__ int s_flag, s_fail;
   __shared__ uint32_t s_waves, s_jlo, s_jhi;
@@ -593,28 +596,61 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
     if (it == a.max_iters || (a.tol > 0.f && it == next_check)) {
       // the residual reads every contact: all colours of this sweep first
       if (a.sync && !grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
-      double num = 0.0, den = 0.0;
-      for (uint32_t col = 0; col < ncol; ++col)
-        for (int part = 0; part < 2; ++part)
-          for (uint32_t p = d.bstart[2 * col + part] + tid; p < d.bend[2 * col + part]; p += stride) {
-            Row r = load_row(d, p);
-            Side A, B;
-            load_pair(d, r, A, B);
-            resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, num, den);
-          }
-      double bn = block_sum(num, sh);
-      double bd = block_sum(den, sh);
-      if (threadIdx.x == 0) {
-        __stcg(d.dpart + 2 * blockIdx.x, bn);
-        __stcg(d.dpart + 2 * blockIdx.x + 1, bd);
+      // Summed in an order that no launch shape changes: the colour order in
+      // chunks of kResChunk contacts, each added by one warp (lane l takes
+      // l, l + 32, ..., then a fixed shuffle tree); then every CTA adds the
+      // chunk sums the same way (kResSum threads, fixed strides, fixed
+      // tree), so all CTAs take the same stop decision from the same value.
+      const uint32_t padded = d.ctr[CTR_PADDED];
+      const uint32_t nchunk = (padded + kResChunk - 1u) / kResChunk;
+      const uint32_t lane = threadIdx.x & 31u;
+      for (uint32_t ch = tid >> 5; ch < nchunk; ch += stride >> 5) {
+        double cn = 0.0, cd = 0.0;
+        for (uint32_t q = 0; q < kResChunk; q += 32u) {
+          const uint32_t p = ch * kResChunk + q + lane;
+          if (p >= padded || __ldcg(&d.p_ab[p].x) == 0xFFFFFFFFu) continue;  // padding slot
+          Row r = load_row(d, p);
+          Side A, B;
+          load_pair(d, r, A, B);
+          resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, cn, cd);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          cn += __shfl_down_sync(0xffffffffu, cn, o);
+          cd += __shfl_down_sync(0xffffffffu, cd, o);
+        }
+        if (lane == 0) {
+          __stcg(d.dres + 2 * ch, cn);
+          __stcg(d.dres + 2 * ch + 1, cd);
+        }
       }
       if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
-      if (threadIdx.x == 0) {
-        double tn = 0.0, td = 0.0;
-        for (uint32_t b = 0; b < gridDim.x; ++b) {
-          tn += __ldcg(d.dpart + 2 * b);
-          td += __ldcg(d.dpart + 2 * b + 1);
+      if (threadIdx.x < kResSum) {
+        double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
+        uint32_t ch = threadIdx.x;
+        for (; ch + kResSum < nchunk; ch += 2u * kResSum) {
+          const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
+          const double2 v = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch + kResSum);
+          n0 += u.x; d0 += u.y;
+          n1 += v.x; d1 += v.y;
         }
+        if (ch < nchunk) {
+          const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
+          n0 += u.x; d0 += u.y;
+        }
+        s_rn[threadIdx.x] = n0 + n1;
+        s_rd[threadIdx.x] = d0 + d1;
+      }
+      __syncthreads();
+      for (uint32_t h = kResSum / 2u; h > 0u; h >>= 1) {
+        if (threadIdx.x < h) {
+          s_rn[threadIdx.x] += s_rn[threadIdx.x + h];
+          s_rd[threadIdx.x] += s_rd[threadIdx.x + h];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) {
+        const double tn = s_rn[0], td = s_rd[0];
         resid = (float)(sqrt(tn) / fmax(sqrt(td), 1e-12));
         s_flag = a.tol > 0.f && resid <= a.tol;
         // next check: a fixed period, or the sweep where the geometric decay
