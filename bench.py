@@ -715,7 +715,8 @@ def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dic
     from paper_2011_00459_gb300 import tds
 
     work = make_workload(args, 0)
-    replay = {"shape": {k: launch_cfg[k] for k in ("pgs_blocks", "pgs_sync", "colour_blocks")}}
+    replay = {"shape": {k: launch_cfg[k] for k in ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads",
+                                                   "pgs_per_thread")}}
     with torch.cuda.stream(stream):
         sim, _ = prepare(args, work, tds, S, stream, replay=replay)
         g = sim.g

@@ -391,13 +391,17 @@ tds_status tds_read_radii(tds_scene *s, float *r, uint32_t n);
  * for bit. pgs_blocks: persistent solver CTAs (one per SM at most);
  * pgs_sync: between colours the solver either synchronises each CTA only
  * with the CTAs whose particles it can touch (1, the default) or all CTAs
- * with a grid barrier (0); colour_blocks: persistent colouring CTAs.
+ * with a grid barrier (0); colour_blocks: persistent colouring CTAs;
+ * pgs_threads x pgs_per_thread: the solver CTA's threads and contacts per
+ * thread, one of the compiled shapes 768x1 (the default), 512x2, 640x2,
+ * 512x3 (both 0 keep the current shape).
  * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
  * tds_set_launch_config ignores the max fields; a zero pgs_blocks or
  * colour_blocks keeps the current value. */
 typedef struct {
   int32_t pgs_blocks, pgs_sync, colour_blocks;
   int32_t max_pgs_blocks, max_colour_blocks;
+  int32_t pgs_threads, pgs_per_thread;
 } tds_launch_config;
 tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out);
 tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg);

@@ -65,20 +65,27 @@ def store_cache(key: str, entry: dict, path: str | None = None) -> None:
 
 
 SYNC_MODES = (1, 0)  # neighbour synchronisation, grid barrier
+SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes the library compiles
+KEYS = ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads", "pgs_per_thread")
 
 
 def candidates(cfg: dict, sms: int) -> list:
-    """Solver shapes to time (sync mode x solver CTAs, the colouring CTAs
-    kept), the library's defaults first."""
-    maxp = cfg["max_pgs_blocks"]
-    pgs = sorted({min(maxp, cfg["pgs_blocks"]), min(maxp, max(1, (3 * cfg["pgs_blocks"]) // 4))}, reverse=True)
-    out = [dict(pgs_blocks=cfg["pgs_blocks"], pgs_sync=cfg["pgs_sync"], colour_blocks=cfg["colour_blocks"])]
+    """Solver shapes to time first (sync mode x solver CTA shape, the CTA
+    counts kept), the library's defaults first."""
+    base = {k: cfg[k] for k in KEYS}
+    out = [base]
     for sync in SYNC_MODES:
-        for p in pgs:
-            shape = dict(pgs_blocks=p, pgs_sync=sync, colour_blocks=cfg["colour_blocks"])
+        for t, per in SHAPES:
+            shape = dict(base, pgs_sync=sync, pgs_threads=t, pgs_per_thread=per)
             if shape not in out:
                 out.append(shape)
     return out
+
+
+def block_candidates(cfg: dict, best: dict) -> list:
+    """Fewer solver CTAs on the chosen solver shape."""
+    p = min(cfg["max_pgs_blocks"], max(1, (3 * best["pgs_blocks"]) // 4))
+    return [dict(best, pgs_blocks=p)] if p != best["pgs_blocks"] else []
 
 
 def colour_candidates(cfg: dict, best: dict, sms: int) -> list:
@@ -120,7 +127,7 @@ def tune(sim, steps: int = 3, sweeps: int = 50, use_cache: bool = True, path: st
     key = shape_key(props.name, g.n, len(g.sizes))
     if use_cache:
         hit = load_cache(path).get(key)
-        if hit and all(k in hit.get("shape", {}) for k in ("pgs_blocks", "pgs_sync", "colour_blocks")):
+        if hit and all(k in hit.get("shape", {}) for k in KEYS):
             shape = hit["shape"]
             if shape["pgs_blocks"] <= cfg["max_pgs_blocks"] and shape["colour_blocks"] <= cfg["max_colour_blocks"]:
                 g.set_launch_config(**shape)
@@ -142,7 +149,9 @@ def tune(sim, steps: int = 3, sweeps: int = 50, use_cache: bool = True, path: st
 
     sms = props.multi_processor_count
     try:
-        timed(colour_candidates(cfg, timed(candidates(cfg, sms)), sms))
+        best = timed(candidates(cfg, sms))
+        best = timed(block_candidates(cfg, best)) if block_candidates(cfg, best) else best
+        timed(colour_candidates(cfg, best, sms))
     finally:
         g.set_solver(*saved)
     ms, best = min(results, key=lambda r: r[0])

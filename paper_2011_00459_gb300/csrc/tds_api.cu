@@ -30,13 +30,15 @@ void tds_mlp_adam_launch(float *params, float *grad, float *mom, float *vel, uin
                          cudaStream_t st);
 int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st);
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
-                           uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st);
+                           uint32_t every, int apply_warm, int blocks, int sync, int shape, cudaStream_t st);
+int tds_pgs_shapes();
+void tds_pgs_shape(int i, int *threads, int *per_thread);
 cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
                               int blocks, cudaStream_t st);
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st);
 int tds_launch_cut(const DevPtrs &d, const StepConsts &k, float *heights, uint32_t nh, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
-int tds_pgs_setup(int *threads);
+int tds_pgs_setup();
 int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, uint32_t nz, uint8_t *zone_id,
                          double *sums, tds_aggregate *out, cudaStream_t st);
 size_t tds_aggregate_sums_words();
@@ -127,12 +129,13 @@ struct Extra {  // workspace regions that are not kernel pointers of DevPtrs
 // arguments that the host settings select.
 struct GraphKey {
   int use_prev = -1, warm = -1, recording = -1, timing = -1;
-  int pgs_blocks = -1, pgs_sync = -1, colour_blocks = -1, cutter = -1;
+  int pgs_blocks = -1, pgs_sync = -1, pgs_shape = -1, colour_blocks = -1, cutter = -1;
   uint32_t max_iters = 0, every = 0, impact_iters = 0;
   float tol = -1.f, restitution = -1.f, impact_speed = -1.f;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
-           pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && colour_blocks == o.colour_blocks &&
+           pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && pgs_shape == o.pgs_shape &&
+           colour_blocks == o.colour_blocks &&
            max_iters == o.max_iters && every == o.every && tol == o.tol && impact_iters == o.impact_iters &&
            restitution == o.restitution && impact_speed == o.impact_speed && cutter == o.cutter;
   }
@@ -168,6 +171,7 @@ struct tds_scene {
   bool geo_dirty = true;
   int pgs_blocks = 1, colour_blocks = 1;
   int pgs_sync = 1;       // solver: 1 neighbour synchronisation, 0 grid barrier
+  int pgs_shape = 0;      // solver CTA shape (index of the compiled shapes)
   bool any_cutter = false;
   int max_pgs_blocks = 1, max_colour_blocks = 1;
   uint64_t steps = 0;
@@ -658,8 +662,7 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
   int dev = 0, sms = 0, occ_pgs = 0, occ_col = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int pgs_threads = 0;
-  if (ce == cudaSuccess) occ_pgs = tds_pgs_setup(&pgs_threads);
+  if (ce == cudaSuccess) occ_pgs = tds_pgs_setup();
   if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_col, tds_colour_kernel(), 256, 0);
   if (ce != cudaSuccess || occ_pgs < 1 || occ_col < 1) {
     delete s;
@@ -834,7 +837,7 @@ tds_status enqueue_step(tds_scene *s, cudaEvent_t *E, uint64_t &launches, bool c
   }
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[3], s->st, evf));
   CUDA_TRY(tds_launch_pgs(d, s->k, D.max_iters, D.tol, D.residual_every, use_prev || learned, s->pgs_blocks,
-                          s->pgs_sync, s->st));
+                          s->pgs_sync, s->pgs_shape, s->st));
   launches += 1;
   if (E) CUDA_TRY(cudaEventRecordWithFlags(E[4], s->st, evf));
   launches += tds_launch_finish(d, s->k, s->L.cap, s->st);
@@ -859,6 +862,7 @@ GraphKey graph_key(const tds_scene *s) {
   g.timing = s->timing;
   g.pgs_blocks = s->pgs_blocks;
   g.pgs_sync = s->pgs_sync;
+  g.pgs_shape = s->pgs_shape;
   g.colour_blocks = s->colour_blocks;
   g.impact_iters = s->desc.impact_iters;
   g.restitution = s->desc.restitution;
@@ -1024,6 +1028,7 @@ tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out) {
   out->colour_blocks = s->colour_blocks;
   out->max_pgs_blocks = s->max_pgs_blocks;
   out->max_colour_blocks = s->max_colour_blocks;
+  tds_pgs_shape(s->pgs_shape, &out->pgs_threads, &out->pgs_per_thread);
   return TDS_OK;
 }
 
@@ -1033,9 +1038,29 @@ tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
       cfg->colour_blocks > s->max_colour_blocks || (cfg->pgs_sync != 0 && cfg->pgs_sync != 1))
     return fail(TDS_ERR_INVALID_ARG,
                 "pgs_blocks and colour_blocks must be in [0, max] (0 keeps the value), pgs_sync 0 or 1");
+  int shape = s->pgs_shape;
+  if (cfg->pgs_threads || cfg->pgs_per_thread) {
+    shape = -1;
+    for (int i = 0; i < tds_pgs_shapes(); ++i) {
+      int t = 0, per = 0;
+      tds_pgs_shape(i, &t, &per);
+      if (t == cfg->pgs_threads && per == cfg->pgs_per_thread) shape = i;
+    }
+    if (shape < 0) {
+      std::string known;
+      for (int i = 0; i < tds_pgs_shapes(); ++i) {
+        int t = 0, per = 0;
+        tds_pgs_shape(i, &t, &per);
+        known += (i ? ", " : "") + std::to_string(t) + "x" + std::to_string(per);
+      }
+      return fail(TDS_ERR_INVALID_ARG, "pgs_threads x pgs_per_thread must be a compiled shape (" + known +
+                                           ") or both 0");
+    }
+  }
   if (cfg->pgs_blocks) s->pgs_blocks = cfg->pgs_blocks;
   if (cfg->colour_blocks) s->colour_blocks = cfg->colour_blocks;
   s->pgs_sync = cfg->pgs_sync;
+  s->pgs_shape = shape;
   return TDS_OK;
 }
 

@@ -192,12 +192,30 @@ __device__ __forceinline__ void st_state(float4 *rec, float4 v, float4 w) {
                "f"(v.z), "f"(v.w), "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w)
                : "memory");
 }
-__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
-__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+// Vector arithmetic with every rounding written out (round-to-nearest
+// intrinsics, fused multiply-adds where named): the compiler cannot contract
+// or reorder them, so a computation rounds the same way in every kernel and
+// every instantiation that uses it (the solver's launch shapes give equal
+// results bit for bit).
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) {
+  return make_float3(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) {
+  return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 operator*(float s, float3 a) {
+  return make_float3(__fmul_rn(s, a.x), __fmul_rn(s, a.y), __fmul_rn(s, a.z));
+}
+// a + s b, one fused multiply-add per component
+__device__ __forceinline__ float3 axpy(float s, float3 b, float3 a) {
+  return make_float3(__fmaf_rn(s, b.x, a.x), __fmaf_rn(s, b.y, a.y), __fmaf_rn(s, b.z, a.z));
+}
+__device__ __forceinline__ float dot(float3 a, float3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
 __device__ __forceinline__ float3 cross(float3 a, float3 b) {
-  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+  return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                     __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
 }
 
 // Orthonormal tangent basis of a unit normal, branch-free (Duff, Burgess,
@@ -205,11 +223,11 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 // Basis, Revisited", JCGT 6(1), 2017). The 2-D tangent update is invariant
 // under the choice of basis, since its effective mass is isotropic.
 __device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
-  float sgn = copysignf(1.0f, n.z);
-  float a = -__frcp_rn(sgn + n.z);
-  float b = n.x * n.y * a;
-  t1 = make_float3(1.0f + sgn * n.x * n.x * a, sgn * b, -sgn * n.x);
-  t2 = make_float3(b, sgn + n.y * n.y * a, -n.y);
+  const float sgn = copysignf(1.0f, n.z);
+  const float a = -__frcp_rn(__fadd_rn(sgn, n.z));
+  const float b = __fmul_rn(__fmul_rn(n.x, n.y), a);
+  t1 = make_float3(__fmaf_rn(__fmul_rn(sgn, __fmul_rn(n.x, n.x)), a, 1.0f), __fmul_rn(sgn, b), -__fmul_rn(sgn, n.x));
+  t2 = make_float3(b, __fmaf_rn(__fmul_rn(n.y, n.y), a, sgn), -n.y);
 }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): the colouring

@@ -69,37 +69,39 @@ __device__ __forceinline__ Row load_row(const DevPtrs &d, uint32_t p) {
 }
 
 // Projections on the Coulomb disk / rolling ball of radius bound (a zero
-// bound forces zero).
+// bound forces zero). All solver arithmetic below spells out its rounding
+// (see the vector helpers): every launch shape of the solver computes the
+// same bits.
 __device__ __forceinline__ void disk(float &a, float &b, float bound) {
-  const float m2 = a * a + b * b;
-  if (m2 > bound * bound) {
-    const float s = bound > 0.f ? bound * rsqrtf(m2) : 0.f;
-    a *= s;
-    b *= s;
+  const float m2 = __fmaf_rn(b, b, __fmul_rn(a, a));
+  if (m2 > __fmul_rn(bound, bound)) {
+    const float s = bound > 0.f ? __fmul_rn(bound, rsqrtf(m2)) : 0.f;
+    a = __fmul_rn(a, s);
+    b = __fmul_rn(b, s);
   }
 }
 __device__ __forceinline__ void ball(float3 &a, float bound) {
   const float m2 = dot(a, a);
-  if (m2 > bound * bound) a = (bound > 0.f ? bound * rsqrtf(m2) : 0.f) * a;
+  if (m2 > __fmul_rn(bound, bound)) a = (bound > 0.f ? __fmul_rn(bound, rsqrtf(m2)) : 0.f) * a;
 }
 
 // v += M^-1 G^T dLambda for each row group. A static side has zero inverse
 // mass and inertia, so its (discarded) update is a no-op.
 __device__ __forceinline__ void apply_normal(const Row &r, Side &A, Side &B, float dn) {
   const float3 P = dn * r.n;
-  A.v = A.v - A.im * P;
-  B.v = B.v + B.im * P;
+  A.v = axpy(-A.im, P, A.v);
+  B.v = axpy(B.im, P, B.v);
 }
 __device__ __forceinline__ void apply_tangent(const Row &r, Side &A, Side &B, float3 dt) {
   const float3 c = cross(r.n, dt);  // torque arms: +la n on a, -lb n on b
-  A.v = A.v - A.im * dt;
-  A.w = A.w - (A.iI * r.la) * c;
-  B.v = B.v + B.im * dt;
-  B.w = B.w - (B.iI * r.lb) * c;
+  A.v = axpy(-A.im, dt, A.v);
+  A.w = axpy(-__fmul_rn(A.iI, r.la), c, A.w);
+  B.v = axpy(B.im, dt, B.v);
+  B.w = axpy(-__fmul_rn(B.iI, r.lb), c, B.w);
 }
 __device__ __forceinline__ void apply_rolling(Side &A, Side &B, float3 dr) {
-  A.w = A.w - A.iI * dr;
-  B.w = B.w + B.iI * dr;
+  A.w = axpy(-A.iI, dr, A.w);
+  B.w = axpy(B.iI, dr, B.w);
 }
 // v += M^-1 G^T (dn, dt(world), dr) on both sides.
 __device__ __forceinline__ void apply(const Row &r, Side &A, Side &B, float dn, float3 dt, float3 dr) {
@@ -111,34 +113,47 @@ __device__ __forceinline__ void apply(const Row &r, Side &A, Side &B, float dn, 
 // Relative velocity of the contact points:
 // (v_b + w_b x (-lb n)) - (v_a + w_a x (la n)) = (v_b - v_a) - (lb w_b + la w_a) x n
 __device__ __forceinline__ float3 slip(const Row &r, const Side &A, const Side &B) {
-  return (B.v - A.v) - cross(r.lb * B.w + r.la * A.w, r.n);
+  return (B.v - A.v) - cross(axpy(r.la, A.w, r.lb * B.w), r.n);
+}
+
+// Diagonal entries of the three row groups: 1/m_a + 1/m_b + Sigma_n,
+// 1/m_a + 1/m_b + la^2/I_a + lb^2/I_b + sigma_t, 1/I_a + 1/I_b + sigma_r.
+__device__ __forceinline__ float diag_n(const Row &r, const Side &A, const Side &B) {
+  return __fadd_rn(__fadd_rn(A.im, B.im), r.Sn);
+}
+__device__ __forceinline__ float diag_t(const Row &r, const Side &A, const Side &B, float sig_t) {
+  const float rot = __fmaf_rn(__fmul_rn(r.lb, r.lb), B.iI, __fmul_rn(__fmul_rn(r.la, r.la), A.iI));
+  return __fadd_rn(__fadd_rn(__fadd_rn(A.im, B.im), rot), sig_t);
+}
+__device__ __forceinline__ float diag_r(const Side &A, const Side &B, float sig_r) {
+  return __fadd_rn(__fadd_rn(A.iI, B.iI), sig_r);
 }
 
 // One projected Gauss-Seidel update of one contact.
 __device__ __forceinline__ void pgs_update(const Row &r, Side &A, Side &B, float4 &L0, float2 &L1,
                                            float sig_t, float sig_r) {
   // normal row
-  const float iDn = __frcp_rn(A.im + B.im + r.Sn);
-  const float res = dot(r.n, B.v - A.v) + r.Sn * L0.x - r.qn;
-  const float ln = fmaxf(L0.x - res * iDn, -r.fc);
-  apply_normal(r, A, B, ln - L0.x);
+  const float iDn = __frcp_rn(diag_n(r, A, B));
+  const float res = __fsub_rn(__fmaf_rn(r.Sn, L0.x, dot(r.n, B.v - A.v)), r.qn);
+  const float ln = fmaxf(__fmaf_rn(-res, iDn, L0.x), -r.fc);
+  apply_normal(r, A, B, __fsub_rn(ln, L0.x));
   L0.x = ln;
   // tangent rows (Coulomb disk)
   float3 t1, t2;
   onb(r.n, t1, t2);
-  const float iDt = __frcp_rn(A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t);
+  const float iDt = __frcp_rn(diag_t(r, A, B, sig_t));
   const float3 u = slip(r, A, B);
-  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) * iDt;
-  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) * iDt;
-  disk(y1, y2, r.mu * fabsf(ln));
-  apply_tangent(r, A, B, (y1 - L0.y) * t1 + (y2 - L0.z) * t2);
+  float y1 = __fmaf_rn(-__fmaf_rn(sig_t, L0.y, dot(t1, u)), iDt, L0.y);
+  float y2 = __fmaf_rn(-__fmaf_rn(sig_t, L0.z, dot(t2, u)), iDt, L0.z);
+  disk(y1, y2, __fmul_rn(r.mu, fabsf(ln)));
+  apply_tangent(r, A, B, axpy(__fsub_rn(y2, L0.z), t2, __fsub_rn(y1, L0.y) * t1));
   L0.y = y1;
   L0.z = y2;
   // rolling rows (ball)
-  const float iDr = __frcp_rn(A.iI + B.iI + sig_r);
+  const float iDr = __frcp_rn(diag_r(A, B, sig_r));
   const float3 lr = make_float3(L0.w, L1.x, L1.y);
-  float3 y = lr - iDr * ((B.w - A.w) + sig_r * lr);
-  ball(y, r.rmu * fabsf(ln));
+  float3 y = axpy(-iDr, axpy(sig_r, lr, B.w - A.w), lr);
+  ball(y, __fmul_rn(r.rmu, fabsf(ln)));
   apply_rolling(A, B, y - lr);
   L0.w = y.x;
   L1.x = y.y;
@@ -149,22 +164,23 @@ __device__ __forceinline__ void pgs_update(const Row &r, Side &A, Side &B, float
 __device__ __forceinline__ void resid_terms(const Row &r, const Side &A, const Side &B, float4 L0,
                                             float2 L1, float sig_t, float sig_r, double &num,
                                             double &den) {
-  float wn = dot(r.n, B.v - A.v) + r.Sn * L0.x - r.qn;
-  float pn = fmaxf(L0.x - wn * __frcp_rn(A.im + B.im + r.Sn), -r.fc);
+  const float wn = __fsub_rn(__fmaf_rn(r.Sn, L0.x, dot(r.n, B.v - A.v)), r.qn);
+  const float pn = fmaxf(__fmaf_rn(-wn, __frcp_rn(diag_n(r, A, B)), L0.x), -r.fc);
   float3 t1, t2;
   onb(r.n, t1, t2);
-  float iDt = __frcp_rn(A.im + B.im + r.la * r.la * A.iI + r.lb * r.lb * B.iI + sig_t);
-  float3 u = slip(r, A, B);
-  float y1 = L0.y - (dot(t1, u) + sig_t * L0.y) * iDt;
-  float y2 = L0.z - (dot(t2, u) + sig_t * L0.z) * iDt;
-  disk(y1, y2, r.mu * fabsf(L0.x));
-  float3 lr = make_float3(L0.w, L1.x, L1.y);
-  float3 y = lr - __frcp_rn(A.iI + B.iI + sig_r) * ((B.w - A.w) + sig_r * lr);
-  ball(y, r.rmu * fabsf(L0.x));
-  float e0 = L0.x - pn, e1 = L0.y - y1, e2 = L0.z - y2;
-  float3 e3 = lr - y;
-  num += (double)(e0 * e0 + e1 * e1 + e2 * e2 + dot(e3, e3));
-  den += (double)(L0.x * L0.x + L0.y * L0.y + L0.z * L0.z + dot(lr, lr));
+  const float iDt = __frcp_rn(diag_t(r, A, B, sig_t));
+  const float3 u = slip(r, A, B);
+  float y1 = __fmaf_rn(-__fmaf_rn(sig_t, L0.y, dot(t1, u)), iDt, L0.y);
+  float y2 = __fmaf_rn(-__fmaf_rn(sig_t, L0.z, dot(t2, u)), iDt, L0.z);
+  disk(y1, y2, __fmul_rn(r.mu, fabsf(L0.x)));
+  const float3 lr = make_float3(L0.w, L1.x, L1.y);
+  float3 y = axpy(-__frcp_rn(diag_r(A, B, sig_r)), axpy(sig_r, lr, B.w - A.w), lr);
+  ball(y, __fmul_rn(r.rmu, fabsf(L0.x)));
+  const float e0 = __fsub_rn(L0.x, pn), e1 = __fsub_rn(L0.y, y1), e2 = __fsub_rn(L0.z, y2);
+  const float3 e3 = lr - y;
+  const float l2 = __fmaf_rn(L0.z, L0.z, __fmaf_rn(L0.y, L0.y, __fmul_rn(L0.x, L0.x)));
+  num += (double)__fadd_rn(__fmaf_rn(e2, e2, __fmaf_rn(e1, e1, __fmul_rn(e0, e0))), dot(e3, e3));
+  den += (double)__fadd_rn(l2, dot(lr, lr));
 }
 
 __device__ __forceinline__ void load_pair(const DevPtrs &d, const Row &r, Side &A, Side &B) {
@@ -196,9 +212,13 @@ struct SolveArgs {
 // ---------------------------------------------------------------------------
 // Staging of the contact rows and impulses with bulk copies (TMA)
 // ---------------------------------------------------------------------------
-constexpr int kPgsThreads = 768;
-constexpr int kPerThread = 1;                        // contacts per thread per wave
-constexpr int kWave = kPgsThreads * kPerThread;      // contacts per wave
+// CTA shapes compiled (threads, contacts per thread per wave; a wave is
+// their product); launch configurations choose one by index. Measured on the
+// 1M bed and the batch, one contact per thread over 768 threads is fastest:
+// each colour phase is a latency chain, and a thread's serial updates are a
+// large part of it.
+constexpr int kShapes[][2] = {{768, 1}, {512, 2}, {640, 2}, {512, 3}};
+constexpr int kNumShapes = 4;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
 constexpr uint32_t kResChunk = 256;                  // residual: contacts per chunk of the colour order
@@ -206,9 +226,9 @@ constexpr uint32_t kResSum = 512;                    // residual: threads adding
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
 //              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
 constexpr size_t kRowBytes = 72;
-constexpr size_t kStageBytes = (size_t)kWave * kRowBytes;
-constexpr size_t kPgsSmem = kStages * kStageBytes;
-constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffLa = 48, kOffLb = 64;  // x kWave
+constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffLa = 48, kOffLb = 64;  // x wave size
+__host__ __device__ constexpr size_t stage_bytes(int wave) { return (size_t)wave * kRowBytes; }
+__host__ __device__ constexpr size_t pgs_smem(int wave) { return kStages * stage_bytes(wave); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -262,44 +282,45 @@ __device__ __forceinline__ void seg_chunk(const DevPtrs &d, uint32_t g, uint32_t
   hi = min(lo + q, e);
 }
 
-// One wave of a colour: up to kWave contacts of this CTA's pair chunk
+// One wave of a colour: up to W contacts of this CTA's pair chunk
 // [lo1, hi1), then of its static chunk [lo2, hi2). The pair part n1 sits at
 // stage entries [0, n1), the static part n2 at [n1e, n1e + n2) with n1e = n1
 // rounded up to even (8-byte fields are copied in 16-byte pairs); n1e + n2 <=
-// kWave. Waves of a colour: the pair chunk in kWave pieces, the last one
+// W. Waves of a colour: the pair chunk in W pieces, the last one
 // topped up with static contacts, then the rest of the static chunk.
 struct WaveDesc {
   uint32_t a1, n1, n1e, a2, n2;
 };
 
-__device__ __forceinline__ uint32_t waves_of(uint32_t L1, uint32_t L2) {
-  const uint32_t W1 = (L1 + kWave - 1) / kWave;
+__device__ __forceinline__ uint32_t waves_of(uint32_t L1, uint32_t L2, uint32_t W) {
+  const uint32_t W1 = (L1 + W - 1) / W;
   uint32_t first2 = 0;  // static contacts in the last pair wave
   if (W1 > 0) {
-    const uint32_t n1 = L1 - (W1 - 1) * kWave;
-    first2 = min(L2, (uint32_t)kWave - ((n1 + 1u) & ~1u));
+    const uint32_t n1 = L1 - (W1 - 1) * W;
+    first2 = min(L2, W - ((n1 + 1u) & ~1u));
   }
-  return W1 + (L2 - first2 + kWave - 1) / kWave;
+  return W1 + (L2 - first2 + W - 1) / W;
 }
 
-__device__ __forceinline__ WaveDesc wave_desc(uint32_t lo1, uint32_t hi1, uint32_t lo2, uint32_t hi2, uint32_t w) {
+__device__ __forceinline__ WaveDesc wave_desc(uint32_t lo1, uint32_t hi1, uint32_t lo2, uint32_t hi2, uint32_t w,
+                                              uint32_t W) {
   const uint32_t L1 = hi1 - lo1, L2 = hi2 - lo2;
-  const uint32_t W1 = (L1 + kWave - 1) / kWave;
+  const uint32_t W1 = (L1 + W - 1) / W;
   WaveDesc q{0, 0, 0, lo2, 0};
   uint32_t first2 = 0;
   if (W1 > 0) {
-    const uint32_t n1 = L1 - (W1 - 1) * kWave;
-    first2 = min(L2, (uint32_t)kWave - ((n1 + 1u) & ~1u));
+    const uint32_t n1 = L1 - (W1 - 1) * W;
+    first2 = min(L2, W - ((n1 + 1u) & ~1u));
   }
   if (w < W1) {
-    q.a1 = lo1 + w * kWave;
-    q.n1 = min((uint32_t)kWave, L1 - w * kWave);
+    q.a1 = lo1 + w * W;
+    q.n1 = min(W, L1 - w * W);
     q.n1e = (q.n1 + 1u) & ~1u;
     if (w == W1 - 1) q.n2 = first2;
   } else {
-    const uint32_t done = first2 + (w - W1) * kWave;
+    const uint32_t done = first2 + (w - W1) * W;
     q.a2 = lo2 + done;
-    q.n2 = min((uint32_t)kWave, L2 - done);
+    q.n2 = min(W, L2 - done);
   }
   return q;
 }
@@ -319,14 +340,14 @@ struct WaveSeq {
 };
 
 __device__ __forceinline__ void stage_range(const DevPtrs &d, uint32_t p0, uint32_t cnt, uint32_t at,
-                                            unsigned char *stage, unsigned long long *bar) {
+                                            unsigned char *stage, unsigned long long *bar, uint32_t W) {
   const uint32_t cnt2 = (cnt + 1u) & ~1u;  // 8-byte fields copied in pairs (16-byte multiples)
-  bulk_g2s(stage + kOffAb * kWave + 8u * at, d.p_ab + p0, 8u * cnt2, bar);
-  bulk_g2s(stage + kOffRn * kWave + 16u * at, d.p_rn + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffRq * kWave + 16u * at, d.p_rq + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffRm * kWave + 8u * at, d.p_rm + p0, 8u * cnt2, bar);
-  bulk_g2s(stage + kOffLa * kWave + 16u * at, d.p_la + p0, 16u * cnt, bar);
-  bulk_g2s(stage + kOffLb * kWave + 8u * at, d.p_lb + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffAb * W + 8u * at, d.p_ab + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffRn * W + 16u * at, d.p_rn + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRq * W + 16u * at, d.p_rq + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffRm * W + 8u * at, d.p_rm + p0, 8u * cnt2, bar);
+  bulk_g2s(stage + kOffLa * W + 16u * at, d.p_la + p0, 16u * cnt, bar);
+  bulk_g2s(stage + kOffLb * W + 8u * at, d.p_lb + p0, 8u * cnt2, bar);
 }
 
 __device__ __forceinline__ uint32_t range_bytes(uint32_t cnt) {
@@ -335,11 +356,11 @@ __device__ __forceinline__ uint32_t range_bytes(uint32_t cnt) {
 
 __device__ __forceinline__ void issue_wave(const DevPtrs &d, const WaveSeq &q, const uint32_t *lo,
                                            const uint32_t *hi, unsigned char *stage,
-                                           unsigned long long *bar) {
-  const WaveDesc w = wave_desc(lo[2 * q.col], hi[2 * q.col], lo[2 * q.col + 1], hi[2 * q.col + 1], q.w);
+                                           unsigned long long *bar, uint32_t W) {
+  const WaveDesc w = wave_desc(lo[2 * q.col], hi[2 * q.col], lo[2 * q.col + 1], hi[2 * q.col + 1], q.w, W);
   mbar_expect_tx(bar, range_bytes(w.n1) + range_bytes(w.n2));
-  if (w.n1) stage_range(d, w.a1, w.n1, 0, stage, bar);
-  if (w.n2) stage_range(d, w.a2, w.n2, w.n1e, stage, bar);
+  if (w.n1) stage_range(d, w.a1, w.n1, 0, stage, bar, W);
+  if (w.n2) stage_range(d, w.a2, w.n2, w.n1e, stage, bar, W);
 }
 
 // Neighbour synchronisation. Every CTA touches particles only inside its slot
@@ -392,7 +413,10 @@ __device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
 // solved and synchronised; each thread then gathers both sides of its
 // kPerThread contacts (through L2) before solving any of them (contacts of
 // one colour touch disjoint particles).
+template <int kPgsThreads, int kPerThread>
 __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
+  constexpr uint32_t kWave = kPgsThreads * kPerThread;  // contacts per wave
+  constexpr size_t kStageBytes = stage_bytes(kWave);
   if (step_failed(d)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long full[kStages];
@@ -415,7 +439,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   for (uint32_t g = threadIdx.x; g < nseg; g += blockDim.x) seg_chunk(d, g, s_lo[g], s_hi[g]);
   __syncthreads();
   for (uint32_t c = threadIdx.x; c < ncol; c += blockDim.x) {
-    s_nw[c] = waves_of(s_hi[2 * c] - s_lo[2 * c], s_hi[2 * c + 1] - s_lo[2 * c + 1]);
+    s_nw[c] = waves_of(s_hi[2 * c] - s_lo[2 * c], s_hi[2 * c + 1] - s_lo[2 * c + 1], kWave);
     atomicAdd(&s_waves, s_nw[c]);
   }
   if (threadIdx.x == 0) {
@@ -507,7 +531,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
     if (threadIdx.x == 0)
       for (uint32_t k = 0; k < ahead && prod.valid(a.max_iters); ++k) {
         issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
-                   &full[issued % kStages]);
+                   &full[issued % kStages], kWave);
         ++issued;
         prod.advance(s_nw, ncol, a.max_iters);
       }
@@ -537,7 +561,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         const float2 *srm = reinterpret_cast<const float2 *>(stage + kOffRm * kWave);
         const float4 *sla = reinterpret_cast<const float4 *>(stage + kOffLa * kWave);
         const float2 *slb = reinterpret_cast<const float2 *>(stage + kOffLb * kWave);
-        const WaveDesc q = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], w);
+        const WaveDesc q = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], w, kWave);
         Side A[kPerThread], B[kPerThread];
         uint32_t gp[kPerThread];  // colour-order index of each staged contact (or ~0)
         // gathers of every contact of this thread first (disjoint particles)
@@ -582,7 +606,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         ++consumed;
         if (threadIdx.x == 0 && prod.valid(a.max_iters)) {
           issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
-                     &full[issued % kStages]);
+                     &full[issued % kStages], kWave);
           ++issued;
           prod.advance(s_nw, ncol, a.max_iters);
         }
@@ -899,15 +923,30 @@ int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
   return 1;
 }
 
+// The compiled solver kernels, by shape index.
+using PgsKernel = void (*)(DevPtrs, SolveArgs);
+template <int I>
+constexpr PgsKernel pgs_kernel() {
+  return k_pgs<kShapes[I][0], kShapes[I][1]>;
+}
+const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>(), pgs_kernel<2>(), pgs_kernel<3>()};
+
+int tds_pgs_shapes() { return kNumShapes; }
+void tds_pgs_shape(int i, int *threads, int *per_thread) {
+  *threads = kShapes[i][0];
+  *per_thread = kShapes[i][1];
+}
+
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
-                           uint32_t every, int apply_warm, int blocks, int sync, cudaStream_t st) {
+                           uint32_t every, int apply_warm, int blocks, int sync, int shape, cudaStream_t st) {
   SolveArgs a{max_iters, every, tol, k.sig_t, k.sig_r, apply_warm, sync};
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
   if (sync) cudaMemsetAsync(d.prog, 0, sizeof(uint32_t) * kProgStride * (size_t)blocks, st);
   DevPtrs dd = d;
   void *args[] = {&dd, &a};
-  return cudaLaunchCooperativeKernel((const void *)k_pgs, dim3(blocks), dim3(kPgsThreads), args,
-                                     kPgsSmem, st);
+  const int T = kShapes[shape][0];
+  return cudaLaunchCooperativeKernel((const void *)kPgsKernels[shape], dim3(blocks), dim3(T), args,
+                                     pgs_smem(T * kShapes[shape][1]), st);
 }
 
 cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
@@ -922,16 +961,20 @@ cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, fl
 
 // Opt the solver into its shared-memory stages; returns the co-resident
 // blocks per SM for the cooperative launch.
-int tds_pgs_setup(int *threads) {
-  *threads = kPgsThreads;
-  if (cudaFuncSetAttribute((const void *)k_pgs, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kPgsSmem) != cudaSuccess)
-    return 0;
-  int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)k_pgs, kPgsThreads, kPgsSmem) !=
-      cudaSuccess)
-    return 0;
-  return occ;
+int tds_pgs_setup() {
+  int occ_min = 0;
+  for (int i = 0; i < kNumShapes; ++i) {
+    const int T = kShapes[i][0];
+    const size_t smem = pgs_smem(T * kShapes[i][1]);
+    if (cudaFuncSetAttribute((const void *)kPgsKernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return 0;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)kPgsKernels[i], T, smem) != cudaSuccess)
+      return 0;
+    occ_min = i == 0 ? occ : (occ < occ_min ? occ : occ_min);
+  }
+  return occ_min;
 }
 
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st) {

@@ -36,6 +36,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
+SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes compiled (threads, contacts per thread)
 
 
 class TdsError(RuntimeError):
@@ -134,7 +135,8 @@ class Cutter(ctypes.Structure):
 class LaunchConfig(ctypes.Structure):
     _fields_ = [("pgs_blocks", ctypes.c_int32), ("pgs_sync", ctypes.c_int32),
                 ("colour_blocks", ctypes.c_int32), ("max_pgs_blocks", ctypes.c_int32),
-                ("max_colour_blocks", ctypes.c_int32)]
+                ("max_colour_blocks", ctypes.c_int32), ("pgs_threads", ctypes.c_int32),
+                ("pgs_per_thread", ctypes.c_int32)]
 
 
 _lib = None
@@ -477,14 +479,19 @@ class Scene:
         _check(lib().tds_get_launch_config(self.h, ctypes.byref(c)))
         return {k: getattr(c, k) for k, _ in LaunchConfig._fields_}
 
-    def set_launch_config(self, pgs_blocks: int = 0, pgs_sync: int | None = None, colour_blocks: int = 0):
-        """Solver CTAs, solver sync mode (1 neighbour, 0 grid barrier) and
-        colouring CTAs; 0 (or None for the mode) keeps the current value."""
+    def set_launch_config(self, pgs_blocks: int = 0, pgs_sync: int | None = None, colour_blocks: int = 0,
+                          pgs_threads: int = 0, pgs_per_thread: int = 0):
+        """Solver CTAs, solver sync mode (1 neighbour, 0 grid barrier),
+        colouring CTAs and the solver CTA shape (threads x contacts per
+        thread, one of SHAPES); 0 (or None for the mode) keeps the current
+        value."""
         c = LaunchConfig()
         _check(lib().tds_get_launch_config(self.h, ctypes.byref(c)))
         c.pgs_blocks, c.colour_blocks = int(pgs_blocks), int(colour_blocks)
         if pgs_sync is not None:
             c.pgs_sync = int(pgs_sync)
+        if pgs_threads or pgs_per_thread:
+            c.pgs_threads, c.pgs_per_thread = int(pgs_threads), int(pgs_per_thread)
         _check(lib().tds_set_launch_config(self.h, ctypes.byref(c)))
 
     def set_graph(self, enable: bool = True):

@@ -22,7 +22,8 @@ def test_cache_round_trip_and_bad_files(tmp_path, monkeypatch):
     monkeypatch.setenv(A.CACHE_ENV, path)
     assert A.cache_path() == path
     assert A.load_cache() == {}
-    A.store_cache("k1", {"shape": {"pgs_blocks": 152, "pgs_sync": 1, "colour_blocks": 304}, "ms": 1.0})
+    A.store_cache("k1", {"shape": {"pgs_blocks": 152, "pgs_sync": 1, "colour_blocks": 304, "pgs_threads": 768,
+                                   "pgs_per_thread": 1}, "ms": 1.0})
     A.store_cache("k2", {"shape": {"pgs_blocks": 114, "pgs_sync": 0, "colour_blocks": 152}, "ms": 2.0})
     data = A.load_cache()
     assert set(data) == {"k1", "k2"} and data["k2"]["shape"]["pgs_sync"] == 0
@@ -35,18 +36,22 @@ def test_cache_round_trip_and_bad_files(tmp_path, monkeypatch):
 
 def test_candidates_start_with_the_defaults_and_stay_in_limits():
     cfg = {"pgs_blocks": 152, "pgs_sync": 1, "colour_blocks": 608, "max_pgs_blocks": 152,
-           "max_colour_blocks": 1216}
+           "max_colour_blocks": 1216, "pgs_threads": 768, "pgs_per_thread": 1}
     c = A.candidates(cfg, 152)
-    assert c[0] == {"pgs_blocks": 152, "pgs_sync": 1, "colour_blocks": 608}
+    assert c[0] == {k: cfg[k] for k in A.KEYS}
     assert len(c) == len({tuple(sorted(x.items())) for x in c})
     for x in c:
-        assert 1 <= x["pgs_blocks"] <= 152 and x["colour_blocks"] == 608 and x["pgs_sync"] in (0, 1)
+        assert x["pgs_blocks"] == 152 and x["colour_blocks"] == 608 and x["pgs_sync"] in (0, 1)
+        assert (x["pgs_threads"], x["pgs_per_thread"]) in A.SHAPES
     assert {x["pgs_sync"] for x in c} == {0, 1}
+    assert {(x["pgs_threads"], x["pgs_per_thread"]) for x in c} == set(A.SHAPES)
     best = c[-1]
+    bc = A.block_candidates(cfg, best)
+    assert len(bc) == 1 and bc[0]["pgs_blocks"] == 114 and dict(bc[0], pgs_blocks=152) == best
     cc = A.colour_candidates(cfg, best, 152)
     assert cc and all(dict(x, colour_blocks=best["colour_blocks"]) == best for x in cc)
     assert all(1 <= x["colour_blocks"] <= 1216 and x["colour_blocks"] != best["colour_blocks"] for x in cc)
-    assert len(c) + len(cc) <= 12  # the tuner times them inside a settle reserve of 80 steps
-    small = A.candidates({"pgs_blocks": 3, "pgs_sync": 0, "colour_blocks": 608, "max_pgs_blocks": 152,
-                          "max_colour_blocks": 1216}, 152)
-    assert min(x["pgs_blocks"] for x in small) >= 1
+    assert len(c) + len(bc) + len(cc) <= 14  # the tuner times them inside a settle reserve of 80 steps
+    small = A.candidates(dict(cfg, pgs_blocks=3, pgs_sync=0), 152)
+    assert all(x["pgs_blocks"] == 3 for x in small)
+    assert A.block_candidates(dict(cfg, pgs_blocks=1), dict(small[0], pgs_blocks=1)) == []

@@ -191,7 +191,8 @@ def test_phase_timing_under_graph_replay(tds):
                                           (False, (2000, 1e-4, 0)), (True, (2000, 1e-4, 0))])
 def test_launch_shapes_give_identical_results(tds, graph, solver):
     """Neighbour synchronisation vs grid barrier, fewer solver and colouring
-    CTAs: every launch shape gives the same states and impulses bit for bit
+    CTAs, every compiled solver CTA shape (threads x contacts per thread):
+    every launch shape gives the same states and impulses bit for bit
     (a batch of uneven beds, moving tools; residual checks every 5 sweeps of
     40, or solved to the 1e-4 residual with adaptive checks, where the
     residual's value decides the sweep count and must not depend on the
@@ -200,7 +201,9 @@ def test_launch_shapes_give_identical_results(tds, graph, solver):
 
     beds = S.batched(5, scenes=5, n_lo=800, n_hi=4000)
     shapes = [dict(pgs_sync=1), dict(pgs_sync=0), dict(pgs_sync=1, pgs_blocks=7, colour_blocks=13),
-              dict(pgs_sync=0, pgs_blocks=3)]
+              dict(pgs_sync=0, pgs_blocks=3), dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=3),
+              dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=2, pgs_blocks=5),
+              dict(pgs_sync=0, pgs_threads=640, pgs_per_thread=2)]
     out = []
     for shape in shapes:
         b = tds.Batch(beds, stream=torch.cuda.Stream())
@@ -220,6 +223,8 @@ def test_launch_shapes_give_identical_results(tds, graph, solver):
         st = b.stats()
         b.close()
         assert cfg["pgs_sync"] == shape["pgs_sync"]
+        if "pgs_threads" in shape:
+            assert (cfg["pgs_threads"], cfg["pgs_per_thread"]) == (shape["pgs_threads"], shape["pgs_per_thread"])
         out.append((c, x, (st["sweep_contacts_pp"], st["sweep_contacts_static"], st["residual"])))
     c0, x0, s0 = out[0]
     if solver[1] > 1e-6:
@@ -232,6 +237,15 @@ def test_launch_shapes_give_identical_results(tds, graph, solver):
         for q in range(len(beds)):
             for key in ("x", "v", "w"):
                 assert np.array_equal(x[q][key], x0[q][key]), (q, key)
+
+
+def test_launch_config_rejects_a_shape_that_is_not_compiled(tds):
+    b = tds.Batch(S.batched(6, scenes=2, n_lo=800, n_hi=900))
+    with pytest.raises(tds.TdsError):
+        b.set_launch_config(pgs_threads=100, pgs_per_thread=1)
+    cfg = b.launch_config()
+    assert (cfg["pgs_threads"], cfg["pgs_per_thread"]) == tds.SHAPES[0]
+    b.close()
 
 
 def test_autotuner_picks_a_candidate_and_caches_it(tds, tmp_path):
