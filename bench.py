@@ -665,11 +665,12 @@ def run_tds(args, rank: int, world: int, local_rank: int):
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = None):
+def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = None, warmup: int = 0):
     """A column of the same bed (same radii, material, sweeps), spawned by the
     same lattice generator over a 0.5 x 0.5 m footprint of the same height,
-    settled by the oracle itself (untimed), then timed for steps of the full
-    sweep count. Returns (particle-steps/s, description, steps timed)."""
+    settled by the oracle itself (untimed), ``warmup`` untimed steps of the
+    full solve, then timed for steps of the full solve. Returns
+    (particle-steps/s, description, steps timed)."""
     from oracle import oracle
     from paper_2011_00459_gb300 import scenes as S
 
@@ -689,6 +690,8 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
     st = oracle.State(col)
     for _ in range(60):  # settle (untimed) with fewer sweeps
         oracle.step(col, st, iters=20)
+    for _ in range(warmup):  # untimed steps of the full solve
+        oracle.step(col, st)
     t0 = time.perf_counter()
     k = 0
     while True:
@@ -698,7 +701,8 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
         if (steps is not None and k >= steps) or (steps is None and el >= seconds):
             break
     desc = (f"FP64 oracle, 1 thread: {n}-sphere column (0.5x0.5 m footprint) of the same bed, "
-            f"oracle-settled 60 steps untimed, then {k} steps timed, PGS to {_solve_desc(scene)}")
+            f"oracle-settled 60 steps and {warmup} full steps untimed, then {k} steps timed, "
+            f"PGS to {_solve_desc(scene)}")
     return n * k / el, desc, k
 
 
@@ -796,7 +800,7 @@ def run_reference(args, rank: int, world: int):
     work = make_workload(args, 0)
     scene = sample_scene(work)
     steps = max(1, args.steps)
-    val, desc, k = oracle_sample(scene, 0.0, args.seed, steps=steps)
+    val, desc, k = oracle_sample(scene, 0.0, args.seed, steps=steps, warmup=args.warmup)
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
            "n_gpus": args.gpus, "steps": k, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -886,7 +890,7 @@ def main():
         from oracle import oracle
 
         oracle.build()
-        val, desc, _ = oracle_sample(sample_scene(work), args.cpu_seconds, args.seed)
+        val, desc, _ = oracle_sample(sample_scene(work), args.cpu_seconds, args.seed, warmup=args.warmup)
         result["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                                   "sample": desc}
     if rank == 0:
