@@ -106,3 +106,39 @@ def test_batch_descriptions_are_checked_on_the_host(L):
     assert L.tds_set_graph(None, 1) == -1
     assert L.tds_batch_set_tool_poses(None, None, 0) == -1
     del ka, kb
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    compiler gives the header's declaration (a C program built from
+    include/tds.h prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2011_00459_gb300 import tds
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    pairs = {"tds_scene_desc": tds.SceneDesc, "tds_step_stats": tds.StepStats, "tds_zone": tds.Zone,
+             "tds_aggregate": tds.Aggregate, "tds_grid": tds.Grid, "tds_cutter": tds.Cutter,
+             "tds_launch_config": tds.LaunchConfig}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "tds.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
