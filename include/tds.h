@@ -385,6 +385,30 @@ tds_status tds_read_heightfield(tds_scene *s, uint32_t scene, float *heights, fl
 /* Radii of all particles by id (0: a dormant slot). Waits. */
 tds_status tds_read_radii(tds_scene *s, float *r, uint32_t n);
 
+/* ---- checkpoint / resume ------------------------------------------------------
+ * The state a step carries into the next, as one host buffer: particle
+ * positions, radii, velocities and spins (in the library's slot order), the
+ * warm-start memory of the last step, the heightfield with its pending mass
+ * and highest heights, each scene's tool pose and the step count. A scene
+ * created from the same descriptions (same particle count, contact capacity,
+ * heightfields and scenes) that loads it continues exactly as the saved one
+ * would have: the same steps give the same results bit for bit. Settings
+ * (solver, warm-start mode and network weights, cutters, impact stage, launch
+ * shapes, graph replay) are not part of the state: set them again.
+ * tds_state_bytes: the buffer size. tds_save_state: waits for the scene's
+ * stream and copies the state of the last completed step into buf (caller
+ * owned, at least tds_state_bytes); a latched device error is returned
+ * instead (and rolls the scene back, see above). tds_load_state: checks the
+ * buffer's header (TDS_ERR_INVALID_ARG for another layout or a foreign
+ * buffer), then replaces the scene's state; statistics and the contacts of
+ * tds_read_contacts stay those of the scene's own last step. The layout: a
+ * 32-byte header (magic "TDSS", version, particles, capacity, heights,
+ * scenes, steps, warm-start flag), 13 floats of tool pose per scene, then the
+ * device arrays in a fixed order. */
+tds_status tds_state_bytes(tds_scene *s, uint64_t *bytes);
+tds_status tds_save_state(tds_scene *s, void *buf, uint64_t bytes);
+tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
+
 /* ---- launch shapes ------------------------------------------------------------
  * Knobs of the GPU schedule (the paper, a CPU method, has none). Results do
  * not depend on them: every setting gives the same impulses and states bit

@@ -945,6 +945,39 @@ tds_status read_particles_impl(tds_scene *s, uint32_t off, uint32_t count, float
   return sync_and_check(s);
 }
 
+// ---- checkpoint / resume -------------------------------------------------
+// What a step carries into the next: particle records in slot order, the
+// warm-start memory written by the last step (buffer 0 after its swap), the
+// heightfield with its pending mass and highest heights, the tool poses and
+// the step count. Everything else is rebuilt by every step.
+struct StateHeader {
+  uint32_t magic, version, n, cap, nheights, nscenes;
+  uint64_t steps;
+  uint32_t have_prev, reserved;
+};
+constexpr uint32_t kStateMagic = 0x53534454u;  // "TDSS"
+constexpr uint32_t kStateVersion = 1u;
+
+struct StatePart {
+  void *dev;
+  size_t bytes;
+};
+
+std::vector<StatePart> state_parts(tds_scene *s) {
+  DevPtrs &d = s->d;
+  const size_t n = s->L.n, cap = s->L.cap, nh = s->L.nheights;
+  return {{d.pos, 16 * n},           {d.pv, 32 * n},           {d.pid, 4 * n},
+          {d.sid, 4 * n},            {d.prev_first[0], 4 * n}, {d.prev_cnt[0], 4 * n},
+          {d.prev_other[0], 4 * cap}, {d.prev_l0[0], 16 * cap}, {d.prev_l1[0], 16 * cap},
+          {s->x.heights, 4 * nh},    {d.hf_pend, 4 * nh},      {d.hf_top, 4 * nh}};
+}
+
+uint64_t state_bytes(tds_scene *s) {
+  uint64_t b = sizeof(StateHeader) + 13 * sizeof(float) * (uint64_t)s->scenes.size();
+  for (const StatePart &p : state_parts(s)) b += p.bytes;
+  return b;
+}
+
 }  // namespace
 
 // Lets other translation units of the library report through tds_last_error.
@@ -991,6 +1024,76 @@ tds_status tds_batch_set_tool_poses(tds_scene *s, const float *poses, uint32_t c
     tds_status r = set_pose_impl(s, q, p, p + 3, p + 7, p + 10);
     if (r != TDS_OK) return r;
   }
+  return TDS_OK;
+}
+
+tds_status tds_state_bytes(tds_scene *s, uint64_t *bytes) {
+  if (!s || !bytes) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  *bytes = state_bytes(s);
+  return TDS_OK;
+}
+
+tds_status tds_save_state(tds_scene *s, void *buf, uint64_t bytes) {
+  if (!s || !buf) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < state_bytes(s)) return fail(TDS_ERR_INVALID_ARG, "buffer smaller than tds_state_bytes()");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  tds_status r = sync_and_check(s);  // the state of the last completed step
+  if (r != TDS_OK) return r;
+  unsigned char *o = static_cast<unsigned char *>(buf);
+  StateHeader h{kStateMagic, kStateVersion, s->L.n, s->L.cap, s->L.nheights, (uint32_t)s->scenes.size(),
+                s->steps, s->have_prev ? 1u : 0u, 0u};
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  for (const SceneHost &q : s->scenes) {
+    float pose[13];
+    std::memcpy(pose, q.pos, 12);
+    std::memcpy(pose + 3, q.quat, 16);
+    std::memcpy(pose + 7, q.vel, 12);
+    std::memcpy(pose + 10, q.angvel, 12);
+    std::memcpy(o, pose, sizeof pose);
+    o += sizeof pose;
+  }
+  for (const StatePart &p : state_parts(s)) {
+    CUDA_TRY(cudaMemcpyAsync(o, p.dev, p.bytes, cudaMemcpyDeviceToHost, s->st));
+    o += p.bytes;
+  }
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  return TDS_OK;
+}
+
+tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes) {
+  if (!s || !buf) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (bytes < sizeof(StateHeader)) return fail(TDS_ERR_INVALID_ARG, "buffer too small for a state");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.version != kStateVersion)
+    return fail(TDS_ERR_INVALID_ARG, "not a saved scene state (or another version)");
+  if (h.n != s->L.n || h.cap != s->L.cap || h.nheights != s->L.nheights || h.nscenes != s->scenes.size())
+    return fail(TDS_ERR_INVALID_ARG, "state saved from a scene of another layout (particles, capacity, "
+                                     "heightfield or scene count)");
+  if (bytes < state_bytes(s)) return fail(TDS_ERR_INVALID_ARG, "buffer shorter than the state");
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof h;
+  for (uint32_t q = 0; q < h.nscenes; ++q) {
+    float pose[13];
+    std::memcpy(pose, o, sizeof pose);
+    o += sizeof pose;
+    tds_status r = set_pose_impl(s, q, pose, pose + 3, pose + 7, pose + 10);
+    if (r != TDS_OK) return r;
+  }
+  for (const StatePart &p : state_parts(s)) {
+    CUDA_TRY(cudaMemcpyAsync(p.dev, o, p.bytes, cudaMemcpyHostToDevice, s->st));
+    o += p.bytes;
+  }
+  const int32_t zero = 0;
+  const uint32_t clean = (uint32_t)h.steps;
+  CUDA_TRY(cudaMemcpyAsync(s->d.err, &zero, sizeof zero, cudaMemcpyHostToDevice, s->st));
+  CUDA_TRY(cudaMemcpyAsync(s->d.ctr + CTR_CLEAN, &clean, sizeof clean, cudaMemcpyHostToDevice, s->st));
+  CUDA_TRY(cudaStreamSynchronize(s->st));
+  s->steps = h.steps;
+  s->have_prev = h.have_prev != 0;
+  s->latched = TDS_OK;
   return TDS_OK;
 }
 

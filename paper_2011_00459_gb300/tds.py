@@ -33,7 +33,8 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_batch_set_tool_pose", "tds_batch_read_particles", "tds_batch_read_tool_forces",
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
             "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid",
-            "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii"]
+            "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii",
+            "tds_state_bytes", "tds_save_state", "tds_load_state"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes compiled (threads, contacts per thread)
@@ -155,6 +156,9 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(vp)]
         L.tds_set_tool_pose.argtypes = [vp, _fp, _fp, _fp, _fp]
         L.tds_step.argtypes = [vp, ctypes.c_uint32]
+        L.tds_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.tds_save_state.argtypes = [vp, vp, ctypes.c_uint64]
+        L.tds_load_state.argtypes = [vp, vp, ctypes.c_uint64]
         L.tds_synchronize.argtypes = [vp]
         L.tds_read_particles.argtypes = [vp] + [vp] * 9 + [ctypes.c_uint32]
         L.tds_read_tool_force.argtypes = [vp, _fp, _fp]
@@ -430,6 +434,19 @@ class Scene:
         r = np.empty(self.n, np.float32)
         _check(lib().tds_read_radii(self.h, ctypes.c_void_p(r.ctypes.data), self.n))
         return r
+
+    def save_state(self) -> np.ndarray:
+        """The state of the last completed step as bytes (a checkpoint)."""
+        n = ctypes.c_uint64()
+        _check(lib().tds_state_bytes(self.h, ctypes.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        _check(lib().tds_save_state(self.h, ctypes.c_void_p(buf.ctypes.data), n.value))
+        return buf
+
+    def load_state(self, buf) -> None:
+        """Continue from a checkpoint of a scene with the same layout."""
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(lib().tds_load_state(self.h, ctypes.c_void_p(buf.ctypes.data), buf.size))
 
     def set_warm_start(self, mode: int):
         _check(lib().tds_set_warm_start(self.h, int(mode)))
