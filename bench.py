@@ -743,6 +743,46 @@ def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dic
             "final_residual": st["residual"], "steps": f"the same steps as {same_as} (identical preparation)"}
 
 
+def paired_learned(args, launch_cfg, stream, same_as: str = "the headline") -> dict:
+    """The learned warm start against the previous-step one from identical
+    states: at every step of the trajectory the state is saved, the step is
+    taken with the network's initial impulses (its sweeps recorded), the state
+    is restored and the step is taken with the previous-step ones (the
+    trajectory continues from there). Untimed: sweeps only."""
+    import torch
+
+    from paper_2011_00459_gb300 import learned as LR
+    from paper_2011_00459_gb300 import scenes as S
+    from paper_2011_00459_gb300 import tds
+
+    work = make_workload(args, 0)
+    replay = {"shape": {k: launch_cfg[k] for k in ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads",
+                                                   "pgs_per_thread")}}
+    sweeps = lambda st: (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"])
+    with torch.cuda.stream(stream):
+        sim, _ = prepare(args, work, tds, S, stream, replay=replay)
+        g = sim.g
+        g.set_mlp_weights(LR.load_weights())
+        prev, learned = [], []
+        for _ in range(args.steps):
+            saved = g.save_state()
+            g.set_warm_start(tds.WARM_LEARNED)
+            g.stats()
+            sim.advance()
+            learned.append(sweeps(g.stats()))
+            g.load_state(saved)
+            sim.k -= 1
+            g.set_warm_start(tds.WARM_PREV)
+            sim.advance()
+            prev.append(sweeps(g.stats()))
+        g.close()
+    p, l = np.array(prev), np.array(learned)
+    return {"steps": f"{args.steps} steps of {same_as}'s trajectory, each solved from the same state both ways",
+            "mean_sweeps_previous_step": float(p.mean()), "mean_sweeps_learned": float(l.mean()),
+            "sweeps_saved": float(1.0 - l.sum() / p.sum()),
+            "steps_fewer": int((l < p).sum()), "steps_more": int((l > p).sum())}
+
+
 def batched_args(args):
     import copy
 
@@ -874,6 +914,10 @@ def main():
             result["forms"]["learned"] = learned_form(args, launch_cfg, torch.cuda.Stream())
         except Exception as exc:  # a form that cannot run is reported, not fatal
             result["forms"]["learned"] = {"error": repr(exc)}
+        try:
+            result["forms"]["learned_paired"] = paired_learned(args, launch_cfg, torch.cuda.Stream())
+        except Exception as exc:
+            result["forms"]["learned_paired"] = {"error": repr(exc)}
         if args.workload == "large":
             try:
                 result["forms"]["batched"], bcfg = batched_form(args, rank, world, local_rank)
@@ -882,6 +926,11 @@ def main():
             except Exception as exc:
                 result["forms"].setdefault("batched", {"error": repr(exc)})
                 result["forms"].setdefault("batched_learned", {"error": repr(exc)})
+            try:
+                result["forms"]["batched_learned_paired"] = paired_learned(batched_args(args), bcfg,
+                                                                           torch.cuda.Stream(), "the batched form")
+            except Exception as exc:
+                result["forms"]["batched_learned_paired"] = {"error": repr(exc)}
             try:
                 result["forms"]["batched_vs_unbatched"] = unbatched_form(args, rank, world, local_rank)
             except Exception as exc:
