@@ -180,9 +180,15 @@ def measured_peaks() -> dict:
 
 
 def pgs_source_sha() -> str:
+    """Hash of the solver's code (tds_solve.cu and tds_internal.cuh with
+    comments and blank lines removed): the ncu counters stay valid while it
+    is unchanged."""
     h = hashlib.sha256()
     for f in ("tds_solve.cu", "tds_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2011_00459_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2011_00459_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(line.rstrip() for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -6,8 +6,10 @@
 // colour: within a colour no two contacts share a particle, so all of them
 // are updated in parallel and the result equals sequential Gauss-Seidel in
 // colour-major order. One persistent, co-resident kernel runs the whole
-// solve with a grid barrier between colours: first v = M^-1 (p + G^T
-// lambda_0) from the warm-start impulses, then the sweeps. Per contact and
+// solve, each CTA waiting between colours only for the CTAs whose particles
+// overlap its own (or, as an option, at a grid barrier): first
+// v = M^-1 (p + G^T lambda_0) from the warm-start impulses, then the sweeps,
+// with residual checks where the tolerance asks for them. Per contact and
 // sweep: the normal row (clamped at -f_c), the 2-D tangent rows projected on
 // the Coulomb disk mu |Lambda_n|, the 3 rolling rows projected on the ball
 // rbar mu_r |Lambda_n| (Eqs. signCoul1-3), each followed by
