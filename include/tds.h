@@ -9,15 +9,15 @@
  * interface) together with the terrain surface heightfield (Eq. surface),
  * and returns the soil motion (particles) and the body-particle contact force
  * that is the source of the digging resistance (section "Microscale model").
- * One call of tds_step performs, per time step, the three lines of
- * Algorithm 1 that form the particle step:
- *   "do collision detection"                            -> hash-grid broadphase,
- *       particle-particle / particle-heightfield / particle-box contacts;
- *   "solve the mesoscale MCP using iterative PGS solver" -> colour-sweep
- *       projected Gauss-Seidel on the contact law of Eqs. signCoul1-3 with the
- *       Hertz mapping and the SPOOK stepper (section "Contacting rigid
+ * One call of tds_step performs, per time step, the three parts of the
+ * particle step in Algorithm 1:
+ *   collision detection -> hash-grid broadphase, particle-particle /
+ *       particle-heightfield / particle-box contacts;
+ *   the iterative PGS solve of the mesoscale MCP -> colour-sweep projected
+ *       Gauss-Seidel on the contact law of Eqs. signCoul1-3 with the Hertz
+ *       mapping and the SPOOK stepper (section "Contacting rigid
  *       multibodies");
- *   "update positions x_{i+1} = x_i + dt v_{i+1}".
+ *   the position update x_{i+1} = x_i + dt v_{i+1}.
  *
  * Conventions
  *  - Every call returns a tds_status; nothing throws across the ABI.
@@ -420,12 +420,21 @@ tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
  * thread, one of the compiled shapes 768x1 (the default), 512x2, 640x2,
  * 512x3 (both 0 keep the current shape).
  * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
- * tds_set_launch_config ignores the max fields; a zero pgs_blocks or
- * colour_blocks keeps the current value. */
+ * wait_limit_us: how long [microseconds] any CTA of the step's persistent
+ * kernels waits for other CTAs (a grid barrier, a neighbour's progress flag,
+ * a staged wave) before it gives up: it latches TDS_ERR_BARRIER_TIMEOUT, every
+ * CTA returns, and the next waiting call reports the error and rolls the
+ * scene back (see the conventions above). Default 2 000 000 (2 s); a
+ * healthy step never comes near it. A limit shorter than the waits of a
+ * normal step makes the step fail that way (the rollback path can be
+ * exercised without any fault).
+ * tds_set_launch_config ignores the max fields; a zero pgs_blocks,
+ * colour_blocks or wait_limit_us keeps the current value. */
 typedef struct {
   int32_t pgs_blocks, pgs_sync, colour_blocks;
   int32_t max_pgs_blocks, max_colour_blocks;
   int32_t pgs_threads, pgs_per_thread;
+  int32_t wait_limit_us;
 } tds_launch_config;
 tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out);
 tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg);
@@ -494,15 +503,20 @@ tds_status tds_mlp_adam_step(float *params, float *grad, float *mom, float *vel,
  * x, y, z, radius: device pointers to n floats (particle i at index i);
  * cohesive != 0 adds the cohesive band 0.025 (r_a + r_b) to the reach.
  * keys: device pointer to cap uint64 slots; receives (a << 32) | b for every
- * touching pair a < b, in no particular order (deterministic for equal
- * inputs); count: device pointer to one uint32 that receives the number of
- * pairs (if it exceeds cap, only cap keys were written). stream: a
- * cudaStream_t or NULL. Asynchronous: results are ready when the stream is.
- * n above TDS_NOALLOC_MAX_PARTICLES is rejected with TDS_ERR_CAPACITY.
+ * touching pair a < b, in an order that depends only on the inputs (equal
+ * inputs give the same array, element by element); count: device pointer to
+ * one uint32 that receives the number of pairs (if it exceeds cap, only the
+ * first cap keys of that same order were written). stream: a cudaStream_t or
+ * NULL. Asynchronous: results are ready when the stream is.
+ * n above TDS_NOALLOC_MAX_PARTICLES is rejected with TDS_ERR_CAPACITY; a CUDA
+ * error left pending by an earlier call is reported as TDS_ERR_CUDA (and left
+ * pending) before anything is launched.
  * Calls no cudaMalloc, cudaFree or allocating library routine. The first call
  * on a device looks up the scratch array's device address (with that device
- * current), so make it before any stream capture. All calls share the array:
- * calls whose GPU work overlaps race, so keep them on one stream. */
+ * current) and keeps it, so make it before any stream capture; the kept
+ * address does not survive a reset of the device (cudaDeviceReset). All
+ * calls share the array: calls whose GPU work overlaps race, so keep them on
+ * one stream. */
 #define TDS_NOALLOC_MAX_PARTICLES 65536
 tds_status tds_find_pair_contacts_noalloc(const float *x, const float *y, const float *z,
                                           const float *radius, uint32_t n, int32_t cohesive,

@@ -8,9 +8,8 @@
  * suite, the package smoke check and the benchmark's CPU-baseline leg may
  * load it. It shares no code, header, table or helper with the CUDA library.
  *
- * What one step computes (Algorithm 1, the three lines "do collision
- * detection", "solve the mesoscale MCP using iterative PGS solver" and
- * "update positions"):
+ * What one step computes (the collision detection, PGS solve of the
+ * mesoscale MCP and position update of the particle step, Algorithm 1):
  *   1. contact detection (particle-particle, particle-heightfield,
  *      particle-box) with an FP32 predicate that the CUDA path evaluates
  *      bit-identically;

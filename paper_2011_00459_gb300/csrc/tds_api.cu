@@ -132,8 +132,10 @@ struct GraphKey {
   int pgs_blocks = -1, pgs_sync = -1, pgs_shape = -1, colour_blocks = -1, cutter = -1;
   uint32_t max_iters = 0, every = 0, impact_iters = 0;
   float tol = -1.f, restitution = -1.f, impact_speed = -1.f;
+  unsigned long long wait_ns = 0;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
+           wait_ns == o.wait_ns &&
            pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && pgs_shape == o.pgs_shape &&
            colour_blocks == o.colour_blocks &&
            max_iters == o.max_iters && every == o.every && tol == o.tol && impact_iters == o.impact_iters &&
@@ -694,6 +696,7 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
   Carver c{(char *)s->mem};
   carve(c, s->L, s->d, s->x, 64 * sms);
   s->d.targ = nullptr;
+  s->d.wait_ns = TDS_BARRIER_NS;
   // common constants
   const tds_scene_desc &D = descs[0];
   StepConsts &k = s->k;
@@ -868,6 +871,7 @@ GraphKey graph_key(const tds_scene *s) {
   g.restitution = s->desc.restitution;
   g.impact_speed = s->desc.impact_speed;
   g.cutter = s->any_cutter;
+  g.wait_ns = s->d.wait_ns;
   return g;
 }
 
@@ -1132,15 +1136,18 @@ tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out) {
   out->max_pgs_blocks = s->max_pgs_blocks;
   out->max_colour_blocks = s->max_colour_blocks;
   tds_pgs_shape(s->pgs_shape, &out->pgs_threads, &out->pgs_per_thread);
+  out->wait_limit_us = (int32_t)(s->d.wait_ns / 1000ull);
   return TDS_OK;
 }
 
 tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
   if (!s || !cfg) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
   if (cfg->pgs_blocks < 0 || cfg->pgs_blocks > s->max_pgs_blocks || cfg->colour_blocks < 0 ||
-      cfg->colour_blocks > s->max_colour_blocks || (cfg->pgs_sync != 0 && cfg->pgs_sync != 1))
+      cfg->colour_blocks > s->max_colour_blocks || (cfg->pgs_sync != 0 && cfg->pgs_sync != 1) ||
+      cfg->wait_limit_us < 0)
     return fail(TDS_ERR_INVALID_ARG,
-                "pgs_blocks and colour_blocks must be in [0, max] (0 keeps the value), pgs_sync 0 or 1");
+                "pgs_blocks and colour_blocks must be in [0, max] (0 keeps the value), pgs_sync 0 or 1, "
+                "wait_limit_us >= 0");
   int shape = s->pgs_shape;
   if (cfg->pgs_threads || cfg->pgs_per_thread) {
     shape = -1;
@@ -1162,6 +1169,7 @@ tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
   }
   if (cfg->pgs_blocks) s->pgs_blocks = cfg->pgs_blocks;
   if (cfg->colour_blocks) s->colour_blocks = cfg->colour_blocks;
+  if (cfg->wait_limit_us) s->d.wait_ns = 1000ull * (unsigned long long)cfg->wait_limit_us;
   s->pgs_sync = cfg->pgs_sync;
   s->pgs_shape = shape;
   return TDS_OK;

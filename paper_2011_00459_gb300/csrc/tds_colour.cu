@@ -160,7 +160,7 @@ __global__ void k_colour_rounds(DevPtrs d) {
         }
       }
     }
-    if (!grid_barrier(d.bar, d.err, gen)) return;
+    if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) return;
     if (fc[(round + 1) % 3] == 0u || round > nc) break;
   }
   __syncthreads();

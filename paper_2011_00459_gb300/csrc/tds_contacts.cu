@@ -1,4 +1,4 @@
-// tds_contacts.cu -- "do collision detection" of Algorithm 1 on the GPU and
+// tds_contacts.cu -- the collision-detection line of Algorithm 1 on the GPU and
 // the rows of the contact law for every contact found.
 //
 //  1. sorted-cell broadphase: bin particles in a uniform grid whose cells are

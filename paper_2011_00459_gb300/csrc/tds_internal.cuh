@@ -12,7 +12,8 @@
 #define TDS_NBUCKETS (2 * TDS_MAX_COLOURS)  // (colour, static?) buckets
 #define TDS_TILE 2048                       // contacts per bucketing tile
 #define TDS_ORDER_PAD (4 * TDS_NBUCKETS + 16) // padding slots of the colour order
-#define TDS_BARRIER_NS 2000000000ull        // 2 s limit on any grid-barrier wait
+#define TDS_BARRIER_NS 2000000000ull        // default limit of a wait on other CTAs (2 s); also the
+                                            // fixed limit of a CTA's wait for its own bulk copies
 
 // Error codes latched on the device (the tds_status values).
 #define DEV_ERR_CAPACITY (-4)
@@ -135,6 +136,8 @@ struct DevPtrs {
   uint32_t *prev_first[2], *prev_cnt[2], *prev_other[2];
   float4 *prev_l0[2], *prev_l1[2];
   // scalars and scratch
+  unsigned long long wait_ns; // limit of every wait on other CTAs (grid barriers, neighbour flags,
+                              // staged waves) before the wait gives up and latches DEV_ERR_BARRIER
   int32_t *err;
   uint32_t *ctr;              // see CTR_* below
   unsigned long long *acc;    // see ACC_* below (sums over steps, reset by the host)
@@ -262,9 +265,11 @@ __device__ __forceinline__ void latch_error(int32_t *err, int32_t code) {
 // semantics (publishing the block's writes, ordered by the preceding
 // __syncthreads) without waiting for a reply, then polls with acquire loads
 // until the counter reaches (gen + 1) x gridDim.x. The wait is bounded: past
-// TDS_BARRIER_NS, or when another block latched an error, it returns false
-// (latching DEV_ERR_BARRIER on a timeout) and the caller must return.
-__device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err, uint32_t &gen) {
+// limit_ns, or when another block latched an error, it returns false
+// (latching DEV_ERR_BARRIER on a timeout) in every thread of the block, and
+// the caller must return.
+__device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err, uint32_t &gen,
+                                             unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -280,7 +285,7 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *bar, int32_t *err, uint32
         if (*(volatile int32_t *)err != 0) { ok = 0; break; }
         unsigned long long t = global_ns();
         if (t0 == 0) t0 = t;
-        else if (t - t0 > TDS_BARRIER_NS) {
+        else if (t - t0 > limit_ns) {
           latch_error(err, DEV_ERR_BARRIER);
           ok = 0;
           break;

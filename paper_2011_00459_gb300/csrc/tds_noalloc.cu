@@ -20,7 +20,12 @@
 //    start at zero (the cell counters) is cleared by each call on its stream.
 //  * Calls whose GPU work overlaps (on different streams, or from different
 //    host threads) race on the array; serialize them on one stream.
+//  * The cached address belongs to the device's primary context: after the
+//    caller resets the device (cudaDeviceReset), it is stale.
+//  * The order of the output keys depends only on the input: every cell's
+//    particles are sorted by index, whatever its size.
 #include <mutex>
+#include <string>
 
 #include "tds_internal.cuh"
 
@@ -149,18 +154,68 @@ __global__ void k_scatter(View v, uint32_t n) {
     v.perm()[atomicAdd(v.cursor() + v.cell_of()[i], 1u)] = i;
 }
 
-// Reproducible order inside each cell: ascending particle index.
+// Reproducible order inside each cell, whatever the order of the atomic
+// scatter: ascending particle index. Cells of up to kSmallCell particles are
+// sorted by one thread each (insertion sort), larger ones by k_cell_sort_big.
+constexpr uint32_t kSmallCell = 64;
+
 __global__ void k_cell_sort(View v) {
   const Plan P = *v.plan();
   const uint32_t ncells = (uint32_t)P.gnx * P.gny * P.gnz;
   uint32_t *perm = v.perm();
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
     uint32_t s = v.cell_start()[c], e = v.cell_start()[c + 1];
-    if (e - s < 2 || e - s > 64) continue;
+    if (e - s < 2 || e - s > kSmallCell) continue;
     for (uint32_t a = s + 1; a < e; ++a) {
       uint32_t val = perm[a], b = a;
       while (b > s && perm[b - 1] > val) { perm[b] = perm[b - 1]; --b; }
       perm[b] = val;
+    }
+  }
+}
+
+// Cells with more than kSmallCell particles (a grid that k_plan coarsened
+// because of a far outlier puts thousands of particles in one cell): one
+// block per cell sorts its m entries in place with a bitonic network in the
+// form whose every comparator puts the smaller value at the lower index
+// (each merge stage starts by comparing mirrored positions of its blocks,
+// then halves). Comparators that reach past m are skipped, which is the same
+// as padding the sequence to a power of two with values larger than any
+// index. Every block walks the cells in a fixed stride; all threads of a
+// block read the same bounds, so the block decides together.
+__global__ void __launch_bounds__(1024) k_cell_sort_big(View v) {
+  const Plan P = *v.plan();
+  const uint32_t ncells = (uint32_t)P.gnx * P.gny * P.gnz;
+  uint32_t *perm = v.perm();
+  for (uint32_t c = blockIdx.x; c < ncells; c += gridDim.x) {
+    const uint32_t s = v.cell_start()[c], e = v.cell_start()[c + 1];
+    const uint32_t m = e - s;
+    if (m <= kSmallCell) continue;
+    uint32_t *a = perm + s;
+    uint32_t pow2 = 1;
+    while (pow2 < m) pow2 <<= 1;
+    const uint32_t half = pow2 >> 1;
+    for (uint32_t k = 2; k <= pow2; k <<= 1) {
+      const uint32_t hk = k >> 1;
+      for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {  // mirrored pairs of each k-block
+        const uint32_t blk = t / hk, x = t % hk;
+        const uint32_t i = blk * k + x, j = blk * k + (k - 1u - x);
+        if (j < m) {
+          const uint32_t ai = a[i], aj = a[j];
+          if (ai > aj) { a[i] = aj; a[j] = ai; }
+        }
+      }
+      __syncthreads();
+      for (uint32_t d = k >> 2; d > 0; d >>= 1) {  // half-cleaners at distance d
+        for (uint32_t t = threadIdx.x; t < half; t += blockDim.x) {
+          const uint32_t i = (t / d) * 2u * d + (t % d), j = i + d;
+          if (j < m) {
+            const uint32_t ai = a[i], aj = a[j];
+            if (ai > aj) { a[i] = aj; a[j] = ai; }
+          }
+        }
+        __syncthreads();
+      }
     }
   }
 }
@@ -226,8 +281,15 @@ extern "C" tds_status tds_find_pair_contacts_noalloc(const float *x, const float
   if (n > kMaxN)
     return tds_set_error_message(TDS_ERR_CAPACITY,
                                  "tds_find_pair_contacts_noalloc: n exceeds TDS_NOALLOC_MAX_PARTICLES (65536)");
+  // an error left pending by an earlier call of the caller is reported, and
+  // left pending, rather than blamed on this call's launches
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return tds_set_error_message(TDS_ERR_CUDA, (std::string("tds_find_pair_contacts_noalloc: a CUDA error of an "
+                                                            "earlier call is pending: ") +
+                                                    cudaGetErrorString(e)).c_str());
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 256)
     return tds_set_error_message(TDS_ERR_CUDA, "tds_find_pair_contacts_noalloc: cudaGetDevice failed");
   uint32_t *base;
@@ -246,21 +308,31 @@ extern "C" tds_status tds_find_pair_contacts_noalloc(const float *x, const float
   cudaStream_t st = (cudaStream_t)stream;
   View v{base};
   const unsigned grid = (n + 255) / 256;
-  cudaMemsetAsync(base + kCellCount, 0, sizeof(uint32_t) * (kMaxCells + 1), st);
+  e = cudaMemsetAsync(base + kCellCount, 0, sizeof(uint32_t) * (kMaxCells + 1), st);
+  if (e != cudaSuccess)
+    return tds_set_error_message(TDS_ERR_CUDA, (std::string("tds_find_pair_contacts_noalloc: cudaMemsetAsync: ") +
+                                                    cudaGetErrorString(e)).c_str());
   k_plan<<<1, 1024, 0, st>>>(v, x, y, z, radius, n, cohesive ? 1 : 0);
   k_cells<<<grid, 256, 0, st>>>(v, x, y, z, n);
   tds_scan_exclusive(base + kCellCount, base + kCellStart, kMaxCells, base + kTmp, st);
-  cudaMemcpyAsync(base + kCursor, base + kCellStart, sizeof(uint32_t) * kMaxCells,
-                  cudaMemcpyDeviceToDevice, st);
+  e = cudaMemcpyAsync(base + kCursor, base + kCellStart, sizeof(uint32_t) * kMaxCells,
+                      cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess)
+    return tds_set_error_message(TDS_ERR_CUDA, (std::string("tds_find_pair_contacts_noalloc: cudaMemcpyAsync: ") +
+                                                    cudaGetErrorString(e)).c_str());
   k_scatter<<<grid, 256, 0, st>>>(v, n);
   k_cell_sort<<<kMaxCells / 256, 256, 0, st>>>(v);
+  k_cell_sort_big<<<128, 1024, 0, st>>>(v);
   k_gather<<<grid, 256, 0, st>>>(v, x, y, z, radius, n);
   k_pairs<false><<<(n + 127) / 128, 128, 0, st>>>(v, n, nullptr, 0);
   tds_scan_exclusive(base + kCnt, base + kCStart, n, base + kTmp, st);
   k_pairs<true><<<(n + 127) / 128, 128, 0, st>>>(v, n, reinterpret_cast<unsigned long long *>(keys), cap);
   k_total<<<1, 1, 0, st>>>(v, n, count);
+  // the launches above are the only work since the pending-error check on
+  // entry, so an error now is theirs
   e = cudaGetLastError();
   if (e != cudaSuccess)
-    return tds_set_error_message(TDS_ERR_CUDA, cudaGetErrorString(e));
+    return tds_set_error_message(TDS_ERR_CUDA, (std::string("tds_find_pair_contacts_noalloc: launch: ") +
+                                                    cudaGetErrorString(e)).c_str());
   return TDS_OK;
 }

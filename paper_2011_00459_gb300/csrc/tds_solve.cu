@@ -1,5 +1,5 @@
-// tds_solve.cu -- "solve the mesoscale MCP using iterative PGS solver" and
-// "update positions" of Algorithm 1.
+// tds_solve.cu -- the iterative PGS solve of the mesoscale MCP and the
+// position update of the particle step (Algorithm 1).
 //
 // The MCP of the SPOOK stepper (section "Contacting rigid multibodies") is
 // solved by projected Gauss-Seidel on the physical impulses, colour by
@@ -251,17 +251,27 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t pari
       : "memory");
   return ok != 0;
 }
-// Bounded wait for a phase of a stage barrier; false (error latched) on timeout.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err) {
+// Bounded wait of one thread for a phase of a stage barrier; false (error
+// latched) when it has waited longer than limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err,
+                                          unsigned long long limit_ns) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
     if (mbar_test(bar, parity)) return true;
     if (k == 0) t0 = global_ns();
-    if ((k & 15u) == 15u && global_ns() - t0 > TDS_BARRIER_NS) {
+    if ((k & 15u) == 15u && global_ns() - t0 > limit_ns) {
       latch_error(err, DEV_ERR_BARRIER);
       return false;
     }
   }
+}
+// The same for the whole CTA: every thread waits (each acquires the staged
+// data for itself), and all take the same decision, so that no thread leaves
+// the wave loop while others go on to its __syncthreads.
+__device__ __forceinline__ bool mbar_wait_all(unsigned long long *bar, uint32_t parity, int32_t *err,
+                                              unsigned long long limit_ns) {
+  const bool ok = mbar_wait(bar, parity, err, limit_ns);
+  return __syncthreads_and(ok) != 0;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
                                          unsigned long long *bar) {
@@ -388,7 +398,7 @@ __device__ __forceinline__ bool neighbour_wait(const DevPtrs &d, uint32_t jlo, u
         if (*(volatile int32_t *)d.err != 0) { *s_fail = 1; break; }
         unsigned long long t = global_ns();
         if (t0 == 0) t0 = t;
-        else if (t - t0 > TDS_BARRIER_NS) {
+        else if (t - t0 > d.wait_ns) {
           latch_error(d.err, DEV_ERR_BARRIER);
           *s_fail = 1;
           break;
@@ -485,7 +495,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       s_mn[0] = mn;
       s_mx[0] = mx;
     }
-    if (!grid_barrier(d.bar, d.err, gen)) return;
+    if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) return;
     const uint32_t lo = s_mn[0], hi = s_mx[0];
     for (uint32_t j = threadIdx.x; j < gridDim.x; j += blockDim.x) {
       const uint32_t jl = __ldcg(d.rng + 2 * j), jh = __ldcg(d.rng + 2 * j + 1);
@@ -521,7 +531,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
           if (r.dyn) store_side(d, r.ab.y, B);
         }
       }
-      if (!grid_barrier(d.bar, d.err, gen)) return;
+      if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) return;
     }
   }
 
@@ -556,7 +566,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       for (uint32_t w = 0; w < s_nw[col]; ++w) {
         const uint32_t st = consumed % kStages;
         unsigned char *stage = smem + (size_t)st * kStageBytes;
-        if (!mbar_wait(&full[st], (consumed / kStages) & 1u, d.err)) { ok = false; break; }
+        if (!mbar_wait_all(&full[st], (consumed / kStages) & 1u, d.err, d.wait_ns)) { ok = false; break; }
         const uint2 *sab = reinterpret_cast<const uint2 *>(stage + kOffAb * kWave);
         const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
         const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);
@@ -615,13 +625,13 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       }
       if (!ok) break;
       if (a.sync) publish(d, phase);
-      else if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
+      else if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) { ok = false; break; }
     }
     if (!ok) break;
     ++it;
     if (it == a.max_iters || (a.tol > 0.f && it == next_check)) {
       // the residual reads every contact: all colours of this sweep first
-      if (a.sync && !grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
+      if (a.sync && !grid_barrier(d.bar, d.err, gen, d.wait_ns)) { ok = false; break; }
       // Summed in an order that no launch shape changes: the colour order in
       // chunks of kResChunk contacts, each added by one warp (lane l takes
       // l, l + 32, ..., then a fixed shuffle tree); then every CTA adds the
@@ -650,7 +660,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
           __stcg(d.dres + 2 * ch + 1, cd);
         }
       }
-      if (!grid_barrier(d.bar, d.err, gen)) { ok = false; break; }
+      if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) { ok = false; break; }
       if (threadIdx.x < kResSum) {
         double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
         uint32_t ch = threadIdx.x;
@@ -701,10 +711,11 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       if (s_flag) break;
     }
   }
-  // drain the waves still in flight before the CTA exits
+  // drain the waves still in flight before the CTA exits (bulk copies of this
+  // CTA's own: a fixed, generous limit, whatever the limit on waits for others)
   if (threadIdx.x == 0)
     for (uint32_t q = consumed; q < issued; ++q)
-      if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err)) break;
+      if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err, TDS_BARRIER_NS)) break;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const uint32_t nc = d.ctr[CTR_NC];
     d.ctr[CTR_ITERS] = it;
@@ -757,7 +768,7 @@ __global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
   if (mine) atomicAdd(&s_count, mine);
   __syncthreads();
   if (threadIdx.x == 0 && s_count) atomicAdd(d.ctr + CTR_IMPACTS, s_count);
-  if (!grid_barrier(d.bar, d.err, gen)) return;
+  if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) return;
   if (*(volatile uint32_t *)(d.ctr + CTR_IMPACTS) == 0) return;  // the same value in every CTA
   for (uint32_t it = 0; it < a.iters; ++it)
     for (uint32_t col = 0; col < ncol; ++col) {
@@ -778,7 +789,7 @@ __global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
           d.p_il[p] = L0;
           d.p_il2[p] = make_float4(L1.x, L1.y, t.z, t.w);
         }
-      if (!grid_barrier(d.bar, d.err, gen)) return;
+      if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) return;
     }
   for (uint32_t col = 0; col < ncol; ++col)
     for (int part = 0; part < 2; ++part)

@@ -137,7 +137,7 @@ class LaunchConfig(ctypes.Structure):
     _fields_ = [("pgs_blocks", ctypes.c_int32), ("pgs_sync", ctypes.c_int32),
                 ("colour_blocks", ctypes.c_int32), ("max_pgs_blocks", ctypes.c_int32),
                 ("max_colour_blocks", ctypes.c_int32), ("pgs_threads", ctypes.c_int32),
-                ("pgs_per_thread", ctypes.c_int32)]
+                ("pgs_per_thread", ctypes.c_int32), ("wait_limit_us", ctypes.c_int32)]
 
 
 _lib = None
@@ -497,14 +497,15 @@ class Scene:
         return {k: getattr(c, k) for k, _ in LaunchConfig._fields_}
 
     def set_launch_config(self, pgs_blocks: int = 0, pgs_sync: int | None = None, colour_blocks: int = 0,
-                          pgs_threads: int = 0, pgs_per_thread: int = 0):
+                          pgs_threads: int = 0, pgs_per_thread: int = 0, wait_limit_us: int = 0):
         """Solver CTAs, solver sync mode (1 neighbour, 0 grid barrier),
-        colouring CTAs and the solver CTA shape (threads x contacts per
-        thread, one of SHAPES); 0 (or None for the mode) keeps the current
-        value."""
+        colouring CTAs, the solver CTA shape (threads x contacts per
+        thread, one of SHAPES) and the limit of a wait on other CTAs [us];
+        0 (or None for the mode) keeps the current value."""
         c = LaunchConfig()
         _check(lib().tds_get_launch_config(self.h, ctypes.byref(c)))
         c.pgs_blocks, c.colour_blocks = int(pgs_blocks), int(colour_blocks)
+        c.wait_limit_us = int(wait_limit_us)
         if pgs_sync is not None:
             c.pgs_sync = int(pgs_sync)
         if pgs_threads or pgs_per_thread:

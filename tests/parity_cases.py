@@ -33,6 +33,21 @@ def packed_scene(n: int, seed: int, cohesion: float = 1000.0, mu_t: float = 0.6,
     return S.with_particles(p, x, r, v, w)
 
 
+def per_contact_impulse_error(scene: dict, keys, lam_gpu, lam_ref) -> np.ndarray:
+    """|Lambda_gpu - Lambda_ref| of every contact (all 7 components) over its
+    weight scale W = |g| h / (1/m_a + 1/m_b) (1/m_b = 0 for a static side)."""
+    keys = np.asarray(keys, np.uint64)
+    r = np.asarray(scene["r"], np.float64)
+    m = scene["density"] * 4.0 / 3.0 * np.pi * r ** 3
+    a = (keys >> np.uint64(32)).astype(np.int64)
+    lo = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    static = (lo & 0x80000000) != 0
+    inv = 1.0 / m[a] + np.where(static, 0.0, 1.0 / m[np.where(static, 0, lo)])
+    W = np.linalg.norm(scene["gravity"]) * scene["dt"] / inv
+    d = np.linalg.norm(np.asarray(lam_gpu, np.float64) - np.asarray(lam_ref, np.float64), axis=1)
+    return d / W
+
+
 def rel_impulse_error(lam_gpu, lam_ref) -> float:
     ref = np.asarray(lam_ref, np.float64)
     den = float(np.linalg.norm(ref))

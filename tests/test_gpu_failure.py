@@ -97,3 +97,57 @@ def test_every_waiting_call_reports_the_failure_once(tds):
     assert g.stats()["steps"] == 1  # the next call sees the restored scene
     g.synchronize()
     g.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("sync", [1, 0])
+def test_waits_that_run_out_fail_the_step_and_roll_it_back(tds, graph, sync):
+    """Every wait of a CTA on other CTAs (grid barriers, neighbours' progress
+    flags, staged waves) gives up after the scene's wait limit. With the
+    limit set to 1 us, far below the waits of a normal step, the step fails:
+    the next waiting call returns TDS_ERR_BARRIER_TIMEOUT, the scene is back
+    at the state before that step, and with the limit restored it steps on
+    exactly like a scene that never failed (no kernel is left waiting)."""
+    import torch
+
+    from tests.parity_cases import packed_scene
+
+    scene = packed_scene(3000, 31, iters=40)
+
+    def make_packed():
+        g = tds.Scene(scene, stream=torch.cuda.Stream())
+        g.set_graph(graph)
+        g.set_launch_config(pgs_sync=sync)
+        return g
+
+    g = make_packed()
+    g.step(2)
+    assert g.launch_config()["wait_limit_us"] == 2_000_000
+    g.set_launch_config(wait_limit_us=1)
+    failed = None
+    for _ in range(5):  # a step whose waits all end within 1 us is still a valid step
+        before = state(g)
+        steps0 = g.stats()["steps"]
+        g.step(1)
+        try:
+            g.synchronize()
+        except tds.TdsError as e:
+            failed = e
+            break
+    assert failed is not None
+    assert tds.STATUS[failed.status] == "TDS_ERR_BARRIER_TIMEOUT"
+    assert g.stats()["steps"] == steps0
+    after = state(g)
+    for k in ("x", "v", "w"):
+        assert np.array_equal(after[k], before[k]), k
+    g.set_launch_config(wait_limit_us=2_000_000)
+    g.step(2)
+    got = state(g)
+    total = g.stats()["steps"]
+    g.close()
+    ref = make_packed()
+    ref.step(total)
+    want = state(ref)
+    ref.close()
+    for k in ("x", "v", "w"):
+        assert np.array_equal(got[k], want[k]), k
