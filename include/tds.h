@@ -421,8 +421,8 @@ tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
  * 512x3 (both 0 keep the current shape).
  * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
  * wait_limit_us: how long [microseconds] any CTA of the step's persistent
- * kernels waits for other CTAs (a grid barrier, a neighbour's progress flag,
- * a staged wave) before it gives up: it latches TDS_ERR_BARRIER_TIMEOUT, every
+ * kernels waits for other CTAs (a grid barrier, a neighbour's progress flag)
+ * before it gives up: it latches TDS_ERR_BARRIER_TIMEOUT, every
  * CTA returns, and the next waiting call reports the error and rolls the
  * scene back (see the conventions above). Default 2 000 000 (2 s); a
  * healthy step never comes near it. A limit shorter than the waits of a

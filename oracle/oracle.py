@@ -25,7 +25,7 @@ def build(force: bool = False) -> str:
     is evaluated in plain IEEE float, operation by operation)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-               "-fno-fast-math", "-o", _SO, _SRC, "-lm"]
+               "-fno-fast-math", "-fopenmp", "-o", _SO, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
     return _SO
 
@@ -47,7 +47,7 @@ class OrcParams(ctypes.Structure):
         ("tool_pos", ctypes.c_float * 3), ("tool_quat", ctypes.c_float * 4),
         ("tool_vel", ctypes.c_float * 3), ("tool_angvel", ctypes.c_float * 3),
         ("restitution", ctypes.c_double), ("impact_speed", ctypes.c_double),
-        ("impact_iters", ctypes.c_int32),
+        ("impact_iters", ctypes.c_int32), ("threads", ctypes.c_int32),
     ]
 
 
@@ -127,6 +127,7 @@ class Params:
         p.restitution = float(s.get("restitution", 0.0))
         p.impact_speed = float(s.get("impact_speed", 0.0))
         p.impact_iters = int(s.get("impact_iters", 0))
+        p.threads = int(s.get("threads", 1))
         hf = s.get("hf")
         if hf is not None:
             h = _f32(hf["h"]).reshape(-1)

@@ -605,11 +605,11 @@ static void pgs_contact(contact *c, const masses *M, double *v, double *w) {
 }
 
 /* Diagonally scaled natural-map residual (a Jacobi pass; order-free):
- * |Lambda - Pi_B(Lambda - D^-1 w(Lambda))| / max(|Lambda|, 1e-12). */
-static double residual(const contact *C, int nc, const double *v, const double *w) {
-  double num = 0.0, den = 0.0;
-  for (int k = 0; k < nc; ++k) {
-    const contact *c = &C[k];
+ * |Lambda - Pi_B(Lambda - D^-1 w(Lambda))| / max(|Lambda|, 1e-12).
+ * Per contact: e = its squared natural-map entries, l = its squared impulses. */
+static void residual_terms(const contact *c, const double *v, const double *w, double *e_out,
+                           double *l_out) {
+  {
     double va[3], wa[3], vb[3], wb[3];
     side_velocities(c, v, w, va, wa, vb, wb);
     double dv[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
@@ -627,9 +627,31 @@ static double residual(const contact *C, int nc, const double *v, const double *
     double e = (c->ln - pn) * (c->ln - pn);
     for (int i = 0; i < 2; ++i) e += (c->lt[i] - yt[i]) * (c->lt[i] - yt[i]);
     for (int i = 0; i < 3; ++i) e += (c->lr[i] - yr[i]) * (c->lr[i] - yr[i]);
-    num += e;
-    den += c->ln * c->ln + c->lt[0] * c->lt[0] + c->lt[1] * c->lt[1] +
-           c->lr[0] * c->lr[0] + c->lr[1] * c->lr[1] + c->lr[2] * c->lr[2];
+    *e_out = e;
+    *l_out = c->ln * c->ln + c->lt[0] * c->lt[0] + c->lt[1] * c->lt[1] +
+             c->lr[0] * c->lr[0] + c->lr[1] * c->lr[1] + c->lr[2] * c->lr[2];
+  }
+}
+
+/* The sums run over the contacts in key order; with threads > 1 the terms
+ * are computed in parallel (scratch holds 2 nc doubles) and then summed in
+ * that same order, so the value does not depend on the thread count. */
+static double residual(const contact *C, int nc, const double *v, const double *w, int threads,
+                       double *scratch) {
+  double num = 0.0, den = 0.0;
+  if (threads > 1 && scratch) {
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(threads) schedule(static)
+#endif
+    for (int k = 0; k < nc; ++k) residual_terms(&C[k], v, w, &scratch[2 * k], &scratch[2 * k + 1]);
+    for (int k = 0; k < nc; ++k) { num += scratch[2 * k]; den += scratch[2 * k + 1]; }
+  } else {
+    for (int k = 0; k < nc; ++k) {
+      double e, l;
+      residual_terms(&C[k], v, w, &e, &l);
+      num += e;
+      den += l;
+    }
   }
   double d = sqrt(den);
   return sqrt(num) / (d > 1e-12 ? d : 1e-12);
@@ -993,20 +1015,37 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
                      c->lt[0] * c->t1[2] + c->lt[1] * c->t2[2]};
     apply(c, &M, v, w, c->ln, tw0, c->lr);
   }
-  /* 5. PGS sweeps */
+  /* 5. PGS sweeps. With threads > 1 (a timing option of the CPU baseline,
+   *    colour order only) the contacts of one colour are updated by several
+   *    threads: they share no particle, so the result is the serial one bit
+   *    for bit. */
   int it = 0;
   double res = -1.0;
   int every = P->residual_every > 0 ? P->residual_every : 1;
+  int threads = (P->threads > 1 && P->order == 0) ? P->threads : 1;
+  double *rs = threads > 1 ? (double *)malloc(sizeof(double) * 2 * (nc + 1)) : NULL;
+  if (threads > 1 && !rs) { rc = -2; goto done; }
   while (it < P->iters) {
-    for (int k = 0; k < nc; ++k) pgs_contact(&C[order[k]], &M, v, w);
+    if (threads > 1) {
+      for (int col = 0; col < ncol; ++col) {
+        const int lo = cstart[col], hi = cstart[col + 1];
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(threads) schedule(static)
+#endif
+        for (int k = lo; k < hi; ++k) pgs_contact(&C[order[k]], &M, v, w);
+      }
+    } else {
+      for (int k = 0; k < nc; ++k) pgs_contact(&C[order[k]], &M, v, w);
+    }
     ++it;
     if (P->tol > 0.0 && it % every == 0) {
-      res = residual(C, nc, v, w);
+      res = residual(C, nc, v, w, threads, rs);
       if (res <= P->tol) break;
     }
   }
   st->iterations = it;
-  st->residual = residual(C, nc, v, w);
+  st->residual = residual(C, nc, v, w, threads, rs);
+  free(rs);
   /* 6. tool force and torque (soil on tool) */
   for (int k = 0; k < nc; ++k) {
     const contact *c = &C[k];

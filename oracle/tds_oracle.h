@@ -3,8 +3,9 @@
  * particle system of "A multiscale model of terrain dynamics for real-time
  * earthmoving simulation" (Servin, Berglund, Nystedt).
  *
- * TEST INFRASTRUCTURE ONLY. This is a plain, slow, single-threaded FP64
- * restatement of the method, written to judge the CUDA path. Only the test
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow FP64 restatement of the
+ * method (single-threaded unless asked to update the contacts of a colour on
+ * several threads, which gives the same bits), written to judge the CUDA path. Only the test
  * suite, the package smoke check and the benchmark's CPU-baseline leg may
  * load it. It shares no code, header, table or helper with the CUDA library.
  *
@@ -63,6 +64,9 @@ typedef struct {
   double restitution;                 /* e */
   double impact_speed;                /* v_imp [m/s] */
   int32_t impact_iters;               /* sweeps of the impact solve */
+  /* threads updating the contacts of one colour at a time (<= 1: one; a
+   * timing option, the results are the same bit for bit; colour order only) */
+  int32_t threads;
 } orc_params;
 
 typedef struct {

@@ -136,8 +136,8 @@ struct DevPtrs {
   uint32_t *prev_first[2], *prev_cnt[2], *prev_other[2];
   float4 *prev_l0[2], *prev_l1[2];
   // scalars and scratch
-  unsigned long long wait_ns; // limit of every wait on other CTAs (grid barriers, neighbour flags,
-                              // staged waves) before the wait gives up and latches DEV_ERR_BARRIER
+  unsigned long long wait_ns; // limit of every wait on other CTAs (grid barriers, neighbour flags)
+                              // before the wait gives up and latches DEV_ERR_BARRIER
   int32_t *err;
   uint32_t *ctr;              // see CTR_* below
   unsigned long long *acc;    // see ACC_* below (sums over steps, reset by the host)

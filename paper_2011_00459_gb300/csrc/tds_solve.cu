@@ -265,14 +265,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     }
   }
 }
-// The same for the whole CTA: every thread waits (each acquires the staged
-// data for itself), and all take the same decision, so that no thread leaves
-// the wave loop while others go on to its __syncthreads.
-__device__ __forceinline__ bool mbar_wait_all(unsigned long long *bar, uint32_t parity, int32_t *err,
-                                              unsigned long long limit_ns) {
-  const bool ok = mbar_wait(bar, parity, err, limit_ns);
-  return __syncthreads_and(ok) != 0;
-}
+
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
                                          unsigned long long *bar) {
   asm volatile(
@@ -566,7 +559,9 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       for (uint32_t w = 0; w < s_nw[col]; ++w) {
         const uint32_t st = consumed % kStages;
         unsigned char *stage = smem + (size_t)st * kStageBytes;
-        if (!mbar_wait_all(&full[st], (consumed / kStages) & 1u, d.err, d.wait_ns)) { ok = false; break; }
+        // a wait for this CTA's own bulk copies (which complete in
+        // microseconds): the fixed limit, not the limit on waits for others
+        if (!mbar_wait(&full[st], (consumed / kStages) & 1u, d.err, TDS_BARRIER_NS)) { ok = false; break; }
         const uint2 *sab = reinterpret_cast<const uint2 *>(stage + kOffAb * kWave);
         const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
         const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);

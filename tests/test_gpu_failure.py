@@ -103,7 +103,7 @@ def test_every_waiting_call_reports_the_failure_once(tds):
 @pytest.mark.parametrize("sync", [1, 0])
 def test_waits_that_run_out_fail_the_step_and_roll_it_back(tds, graph, sync):
     """Every wait of a CTA on other CTAs (grid barriers, neighbours' progress
-    flags, staged waves) gives up after the scene's wait limit. With the
+    flags) gives up after the scene's wait limit. With the
     limit set to 1 us, far below the waits of a normal step, the step fails:
     the next waiting call returns TDS_ERR_BARRIER_TIMEOUT, the scene is back
     at the state before that step, and with the limit restored it steps on

@@ -527,3 +527,18 @@ def test_mlp_forward_is_the_layer_formula(orc):
     h1 = np.maximum(X @ p["W1"].T + p["b1"], 0)
     h2 = np.maximum(h1 @ p["W2"].T + p["b2"], 0)
     np.testing.assert_allclose(Y, h2 @ p["W3"].T + p["b3"], rtol=1e-12, atol=1e-12)
+
+
+def test_threaded_colour_sweep_is_bitwise_the_serial_one(orc):
+    """The CPU baseline's option of updating a colour's contacts on several
+    threads changes nothing: those contacts share no particle, and the
+    residual is summed in key order either way."""
+    x, r, v, w = S.packed_block(600, 0.02, 0.03, 12)
+    s = S.with_particles(S.base_params(iters=300, tol=1e-4, residual_every=5, cohesion=1000.0,
+                                       hf=S.flat_heightfield(12, 12, 0, 0, 0.05, 0.05)), x, r, v, w)
+    sa, sb = orc.State(s), orc.State(s)
+    ra = orc.step(s, sa)
+    rb = orc.step(s, sb, threads=4)
+    assert ra["iterations"] == rb["iterations"] and ra["residual"] == rb["residual"]
+    assert np.array_equal(ra["lam"], rb["lam"])
+    assert np.array_equal(sa.x, sb.x) and np.array_equal(sa.v, sb.v) and np.array_equal(sa.w, sb.w)
