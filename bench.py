@@ -105,7 +105,7 @@ def parse():
     ap.add_argument("--cold", action="store_true", help="cold start instead of previous-step impulses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true")
     return ap.parse_args()
 
@@ -671,12 +671,35 @@ def run_tds(args, rank: int, world: int, local_rank: int):
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = None, warmup: int = 0):
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu on Arm hosts)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = None, warmup: int = 0,
+                  threads: int = 1):
     """A column of the same bed (same radii, material, sweeps), spawned by the
     same lattice generator over a 0.5 x 0.5 m footprint of the same height,
     settled by the oracle itself (untimed), ``warmup`` untimed steps of the
-    full solve, then timed for steps of the full solve. Returns
-    (particle-steps/s, description, steps timed)."""
+    full solve, then timed for steps of the full solve; ``threads`` > 1
+    updates the contacts of each colour on that many threads (the same
+    results bit for bit). Returns (particle-steps/s, description, steps timed,
+    mean sweeps per timed step)."""
     from oracle import oracle
     from paper_2011_00459_gb300 import scenes as S
 
@@ -700,24 +723,38 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
         oracle.step(col, st)
     t0 = time.perf_counter()
     k = 0
+    sweeps = 0
     while True:
-        oracle.step(col, st)
+        sweeps += oracle.step(col, st, threads=threads)["iterations"]
         k += 1
         el = time.perf_counter() - t0
         if (steps is not None and k >= steps) or (steps is None and el >= seconds):
             break
-    desc = (f"FP64 oracle, 1 thread: {n}-sphere column (0.5x0.5 m footprint) of the same bed, "
+    who = "1 thread" if threads <= 1 else f"{threads} threads (each colour's contacts split among them)"
+    desc = (f"FP64 oracle, {who}: {n}-sphere column (0.5x0.5 m footprint) of the same bed, "
             f"oracle-settled 60 steps and {warmup} full steps untimed, then {k} steps timed, "
-            f"PGS to {_solve_desc(scene)}")
-    return n * k / el, desc, k
+            f"PGS to {_solve_desc(scene)} ({sweeps / k:.1f} sweeps per step)")
+    return n * k / el, desc, k, sweeps / k
 
 
-def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dict:
+def cpu_baseline(scene: dict, seconds: float, seed: int, warmup: int, gpu_sweeps: float | None) -> dict:
+    """The oracle on all host cores (the reported baseline) and on one thread,
+    with the CPU model, the oracle's sweeps per step and the GPU's."""
+    cores = os.cpu_count() or 1
+    val, desc, _, sw = oracle_sample(scene, seconds, seed, warmup=warmup, threads=cores)
+    v1, d1, _, sw1 = oracle_sample(scene, seconds, seed, warmup=warmup, threads=1)
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+            "sweeps_per_step": sw, "gpu_sweeps_per_step": gpu_sweeps, "cpu_model": cpu_model(),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": d1, "sweeps_per_step": sw1}}
+
+
+def learned_form(args, launch_cfg, stream, same_as: str = "the headline", cold: bool = False) -> dict:
     """The learned warm start on the workload of ``args``: an identical
     preparation (same settle, launch shapes, approach and warm-up with the
     previous-step warm start), then the same timed steps with the network
     trained on plain solves of the small and bulldozing beds (weights shipped
-    with the package)."""
+    with the package). ``cold``: the same steps started from zero impulses
+    instead (plain PGS without any warm start)."""
     import torch
 
     from paper_2011_00459_gb300 import learned as LR
@@ -730,8 +767,11 @@ def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dic
     with torch.cuda.stream(stream):
         sim, _ = prepare(args, work, tds, S, stream, replay=replay)
         g = sim.g
-        g.set_mlp_weights(LR.load_weights())
-        g.set_warm_start(tds.WARM_LEARNED)
+        if cold:
+            g.set_warm_start(tds.WARM_COLD)
+        else:
+            g.set_mlp_weights(LR.load_weights())
+            g.set_warm_start(tds.WARM_LEARNED)
         g.stats()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -743,7 +783,8 @@ def learned_form(args, launch_cfg, stream, same_as: str = "the headline") -> dic
         ms = e0.elapsed_time(e1)
         st = g.stats()
         g.close()
-    return {"warm_start": "learned (10-64-64-3 BF16 network)", "value": sim.n * args.steps / (ms * 1e-3),
+    return {"warm_start": "cold (zero impulses)" if cold else "learned (10-64-64-3 BF16 network)",
+            "value": sim.n * args.steps / (ms * 1e-3),
             "unit": UNIT, "ms_per_step": ms / args.steps,
             "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
             "final_residual": st["residual"], "steps": f"the same steps as {same_as} (identical preparation)"}
@@ -828,6 +869,41 @@ def unbatched_form(args, rank: int, world: int, local_rank: int, steps: int = 3)
     return out
 
 
+CONFIG_FORMS = (("small", 1), ("bulldozing", 2), ("excavation", 3))
+
+
+def config_form(args, name: str, rank: int, world: int, local_rank: int, steps: int = 10) -> dict:
+    """Another of the workload's configurations, timed like the headline: the
+    same metric (every step solved to the residual of ``args``, previous-step
+    warm start) and, where the configuration fixes a sweep count, a second
+    region at that count. The excavation configuration adds the same steps
+    from a cold start and with the learned warm start, and the learned warm
+    start paired with the previous-step one from identical states."""
+    import copy
+
+    import torch
+
+    a = copy.copy(args)
+    a.workload, a.n, a.scenes, a.no_e2e, a.no_cpu_baseline = name, 0, 0, True, True
+    a.steps = min(args.steps, steps)
+    a.roofline_sweeps = 0 if name == "excavation" else -1
+    work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(a, rank, world, local_rank)
+    msw = lambda q: (q["sweep_contacts_pp"] + q["sweep_contacts_static"]) / max(1, q["sum_contacts"])
+    out = {"workload": describe(work, a)["workload"], "particles": int(n_all), "steps": a.steps,
+           "warm_start": "previous step", "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT,
+           "ms_per_step": ms / a.steps, "mean_sweeps": msw(st), "final_residual": st["residual"],
+           "contacts_per_step": st["sum_contacts"] / max(1, st["solved_steps"]), "colours": st["n_colours"],
+           "gpu_launches": int(launches)}
+    if fixed:
+        out["fixed_sweeps"] = {"sweeps": fixed["sweeps"], "value": n_all * a.steps / (fixed["ms"] * 1e-3),
+                               "unit": UNIT, "ms_per_step": fixed["ms"] / a.steps}
+    if name == "excavation":
+        out["cold"] = learned_form(a, launch_cfg, torch.cuda.Stream(), "the excavation configuration", cold=True)
+        out["learned"] = learned_form(a, launch_cfg, torch.cuda.Stream(), "the excavation configuration")
+        out["learned_paired"] = paired_learned(a, launch_cfg, torch.cuda.Stream(), "the excavation configuration")
+    return out
+
+
 def sample_scene(work) -> dict:
     """The scene the oracle samples: the bed itself, or the batch's bed of
     median size."""
@@ -846,13 +922,14 @@ def run_reference(args, rank: int, world: int):
     work = make_workload(args, 0)
     scene = sample_scene(work)
     steps = max(1, args.steps)
-    val, desc, k = oracle_sample(scene, 0.0, args.seed, steps=steps, warmup=args.warmup)
+    cores = os.cpu_count() or 1
+    val, desc, k, sw = oracle_sample(scene, 0.0, args.seed, steps=steps, warmup=args.warmup, threads=cores)
     out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
            "n_gpus": args.gpus, "steps": k, "warmup": args.warmup, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": describe(work, args),
-           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": desc},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": desc, "sweeps_per_step": sw, "cpu_model": cpu_model()},
            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -941,13 +1018,18 @@ def main():
                 result["forms"]["batched_vs_unbatched"] = unbatched_form(args, rank, world, local_rank)
             except Exception as exc:
                 result["forms"]["batched_vs_unbatched"] = {"error": repr(exc)}
+            result["configs"] = {}
+            for name, num in CONFIG_FORMS:
+                try:
+                    result["configs"][name] = {"config": num, **config_form(args, name, rank, world, local_rank)}
+                except Exception as exc:
+                    result["configs"][name] = {"config": num, "error": repr(exc)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle
 
         oracle.build()
-        val, desc, _ = oracle_sample(sample_scene(work), args.cpu_seconds, args.seed, warmup=args.warmup)
-        result["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                  "sample": desc}
+        result["cpu_baseline"] = cpu_baseline(sample_scene(work), args.cpu_seconds, args.seed, args.warmup,
+                                              result["config"]["mean_sweeps"])
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

@@ -101,6 +101,7 @@ typedef enum { TDS_WARM_COLD = 0, TDS_WARM_PREV = 1, TDS_WARM_LEARNED = 2 } tds_
  *   from the particles, heightfield and walls.
  */
 #define TDS_MAX_BOXES 24
+#define TDS_MAX_SCENES 4096  /* scenes in one batch */
 
 typedef struct {
   uint32_t n;
@@ -234,9 +235,13 @@ void tds_destroy_scene(tds_scene *s);
  * A batch is a tds_scene handle; the calls above apply to it as a whole:
  * particle ids are global, scene q owning ids [o_q, o_q + n_q) with o_q the
  * sum of the earlier scenes' n; tds_set_tool_pose and tds_read_tool_force
- * address scene 0; statistics are summed over the batch (one solve: the
- * sweep count and residual are the batch's). tds_create_scene is a batch of
- * one. */
+ * address scene 0; statistics are summed over the batch. In residual mode
+ * every scene has its own residual (the natural-map residual of its own
+ * contacts) and stops sweeping at the first check where it is <= tol, as it
+ * would alone; the step ends when every scene has stopped (or at max_iters).
+ * tds_get_stats then reports the most sweeps any scene did and the largest
+ * final residual; tds_batch_read_solve gives each scene's. At most
+ * TDS_MAX_SCENES scenes. tds_create_scene is a batch of one. */
 tds_status tds_batch_workspace_bytes(const tds_scene_desc *descs, uint32_t count, uint64_t *bytes);
 tds_status tds_create_batch(const tds_scene_desc *descs, uint32_t count, void *workspace,
                             uint64_t workspace_bytes, void *stream, tds_scene **out);
@@ -261,6 +266,11 @@ tds_status tds_batch_read_particles(tds_scene *s, uint32_t scene, float *x, floa
 /* Force and torque on every scene's tool during the last step: 6 floats per
  * scene (fx, fy, fz, tx, ty, tz), count = the number of scenes. Waits. */
 tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_t count);
+
+/* Each scene's solve in the last step: its residual at its last check (the
+ * check that stopped it, or the last sweep) and its sweeps; count = the
+ * number of scenes, either pointer may be NULL. Waits. */
+tds_status tds_batch_read_solve(tds_scene *s, float *residual, uint32_t *sweeps, uint32_t count);
 
 /* Replay each step from a CUDA graph (1) or launch its kernels one by one
  * (0, the default). The graph is captured on the next step and captured

@@ -223,6 +223,7 @@ tds_status validate(const tds_scene_desc *d) {
 // Scenes of one batch share the step, material and solver settings.
 tds_status validate_batch(const tds_scene_desc *descs, uint32_t count) {
   if (!descs || count == 0) return fail(TDS_ERR_INVALID_ARG, "descs is NULL or count is 0");
+  if (count > TDS_MAX_SCENES) return fail(TDS_ERR_INVALID_ARG, "more than TDS_MAX_SCENES scenes in a batch");
   uint64_t total = 0;
   for (uint32_t s = 0; s < count; ++s) {
     tds_status v = validate(descs + s);
@@ -421,7 +422,16 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   size_t nd = 2 * (size_t)pgs_blocks;
   if (nd < 6 * 128) nd = 6 * 128;
   d.dpart = c.take<double>(nd);
-  d.dres = c.take<double>(2 * (((size_t)cap + TDS_ORDER_PAD + 255) / 256 + 1));
+  const size_t nsb = (size_t)L.S * TDS_NBUCKETS;
+  const size_t max_chunks = (size_t)cap / TDS_RES_CHUNK + nsb + 1;
+  d.dres = c.take<double>(2 * max_chunks);
+  d.nscenes = L.S;
+  d.scq_cnt = c.take<uint32_t>(nsb);
+  d.scq_start = c.take<uint32_t>(nsb);
+  d.scq_chunk = c.take<uint32_t>(nsb + 1);
+  d.chunk = c.take<uint4>(max_chunks);
+  d.scene_res = c.take<float>(L.S);
+  d.scene_iters = c.take<uint32_t>(L.S);
   d.bar = c.take<uint32_t>(2);
   d.prog = c.take<uint32_t>(kProgStride * (size_t)pgs_blocks);
   d.rng = c.take<uint32_t>(2 * (size_t)pgs_blocks);
@@ -1312,6 +1322,18 @@ tds_status tds_batch_read_tool_forces(tds_scene *s, float *force_torque, uint32_
   tds_status ls = check_latched(s);
   if (ls != TDS_OK) return ls;
   CUDA_TRY(cudaMemcpyAsync(force_torque, s->d.tool_out, sizeof(float) * 6 * count, cudaMemcpyDeviceToHost, s->st));
+  return sync_and_check(s);
+}
+
+tds_status tds_batch_read_solve(tds_scene *s, float *residual, uint32_t *sweeps, uint32_t count) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
+  if (count != s->scenes.size()) return fail(TDS_ERR_INVALID_ARG, "count differs from the batch size");
+  tds_status ls = check_latched(s);
+  if (ls != TDS_OK) return ls;
+  if (residual)
+    CUDA_TRY(cudaMemcpyAsync(residual, s->d.scene_res, sizeof(float) * count, cudaMemcpyDeviceToHost, s->st));
+  if (sweeps)
+    CUDA_TRY(cudaMemcpyAsync(sweeps, s->d.scene_iters, sizeof(uint32_t) * count, cudaMemcpyDeviceToHost, s->st));
   return sync_and_check(s);
 }
 

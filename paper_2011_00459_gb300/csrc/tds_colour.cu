@@ -251,8 +251,60 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(DevPtrs d) {
       if (bk & 1u) { d.p_sv[p] = d.c_sv[c]; d.p_sw[p] = d.c_sw[c]; }
       d.p_la[p] = d.c_la[c];
       d.p_lb[p] = d.c_lb[c];
+      if (d.nscenes > 1) atomicAdd(d.scq_cnt + (size_t)d.sid[d.c_ab[c].x] * TDS_NBUCKETS + bk, 1u);
     }
     __syncthreads();
+  }
+}
+
+// Residual chunks. Inside a bucket the contacts keep the owner order, which
+// is scene-major (slots are sorted by cell, cells by scene), so each scene's
+// contacts of a bucket form one range; its start is the bucket's start plus
+// the contacts of the earlier scenes. Each range is cut into chunks of at
+// most TDS_RES_CHUNK contacts, numbered scene-major (scene, bucket, piece):
+// a scene's chunks are consecutive, and they are the same chunks whether the
+// scene is stepped alone or in a batch. One block.
+__global__ void __launch_bounds__(1024) k_scene_chunks(DevPtrs d) {
+  constexpr uint32_t NB = TDS_NBUCKETS;
+  const uint32_t S = d.nscenes, total = S * NB;
+  __shared__ uint32_t part[1024];
+  for (uint32_t b = threadIdx.x; b < NB; b += blockDim.x) {
+    uint32_t run = d.bstart[b];
+    for (uint32_t q = 0; q < S; ++q) {
+      const size_t e = (size_t)q * NB + b;
+      const uint32_t cnt = S == 1 ? d.bend[b] - d.bstart[b] : d.scq_cnt[e];
+      if (S == 1) d.scq_cnt[e] = cnt;
+      d.scq_start[e] = run;
+      run += cnt;
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the pieces over (scene, bucket): each thread a
+  // contiguous segment, then a scan of the segment sums
+  const uint32_t seg = (total + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(threadIdx.x * seg, total), hi = min(lo + seg, total);
+  uint32_t sum = 0;
+  for (uint32_t e = lo; e < hi; ++e) sum += (d.scq_cnt[e] + TDS_RES_CHUNK - 1u) / TDS_RES_CHUNK;
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t t = 0; t < blockDim.x; ++t) {
+      const uint32_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    d.scq_chunk[total] = run;
+    d.ctr[CTR_NCHUNK] = run;
+  }
+  __syncthreads();
+  uint32_t base = part[threadIdx.x];
+  for (uint32_t e = lo; e < hi; ++e) {
+    d.scq_chunk[e] = base;
+    const uint32_t cnt = d.scq_cnt[e], start = d.scq_start[e], q = e / NB;
+    for (uint32_t k = 0; k * TDS_RES_CHUNK < cnt; ++k)
+      d.chunk[base + k] = make_uint4(start + k * TDS_RES_CHUNK, min(TDS_RES_CHUNK, cnt - k * TDS_RES_CHUNK), q, 0u);
+    base += (cnt + TDS_RES_CHUNK - 1u) / TDS_RES_CHUNK;
   }
 }
 
@@ -286,8 +338,10 @@ int tds_launch_bucketing(const DevPtrs &d, uint32_t cap, cudaStream_t st) {
   k_bucket_starts<<<1, 32, 0, st>>>(d);
   cudaMemsetAsync(d.order, 0xFF, sizeof(uint32_t) * ((size_t)cap + TDS_ORDER_PAD), st);
   cudaMemsetAsync(d.p_ab, 0xFF, sizeof(uint2) * ((size_t)cap + TDS_ORDER_PAD), st);  // padding sentinel
+  if (d.nscenes > 1) cudaMemsetAsync(d.scq_cnt, 0, sizeof(uint32_t) * (size_t)d.nscenes * TDS_NBUCKETS, st);
   k_bucket_scatter<<<d.ntiles, 256, 0, st>>>(d);
-  return 4;
+  k_scene_chunks<<<1, 1024, 0, st>>>(d);
+  return 5;
 }
 
 const void *tds_colour_kernel() { return (const void *)k_colour_rounds; }

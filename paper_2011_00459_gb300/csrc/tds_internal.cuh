@@ -12,6 +12,7 @@
 #define TDS_NBUCKETS (2 * TDS_MAX_COLOURS)  // (colour, static?) buckets
 #define TDS_TILE 2048                       // contacts per bucketing tile
 #define TDS_ORDER_PAD (4 * TDS_NBUCKETS + 16) // padding slots of the colour order
+#define TDS_RES_CHUNK 256u                  // contacts per residual chunk (at most)
 #define TDS_BARRIER_NS 2000000000ull        // default limit of a wait on other CTAs (2 s); also the
                                             // fixed limit of a CTA's wait for its own bulk copies
 
@@ -143,7 +144,16 @@ struct DevPtrs {
   unsigned long long *acc;    // see ACC_* below (sums over steps, reset by the host)
   float *fscal;               // see FS_* below
   double *dpart;              // per-block partial sums
-  double *dres;               // solver residual: per chunk of the colour order (numerator, denominator)
+  double *dres;               // solver residual: per chunk (numerator, denominator)
+  // residual chunks: every (scene, bucket) range of the colour order cut into
+  // pieces of at most kResChunk contacts; a chunk holds one scene's contacts
+  uint32_t nscenes;           // scenes of the batch
+  uint32_t *scq_cnt;          // contacts per (scene, bucket), scene-major
+  uint32_t *scq_start;        // colour-order start of each (scene, bucket) range
+  uint32_t *scq_chunk;        // first chunk of each (scene, bucket), S * TDS_NBUCKETS + 1
+  uint4 *chunk;               // (colour-order start, contacts, scene, 0) per chunk
+  float *scene_res;           // per scene: residual at its last check of the last step
+  uint32_t *scene_iters;      // per scene: sweeps of the last step
   uint32_t *bar;              // grid barrier: [0] arrivals, [1] generation
   uint32_t *prog;             // solver neighbour sync: last colour phase published per CTA,
                               // one flag per kProgStride words (own 128-byte line)
@@ -172,7 +182,7 @@ struct DevPtrs {
 
 enum { CTR_NC = 0, CTR_NCOL = 1, CTR_ITERS = 2, CTR_FCOUNT = 4, /* 4,5,6 */ CTR_NPP = 8,
        CTR_NSTAT = 9, CTR_TOTAL = 10, CTR_ROUNDS = 11, CTR_PADDED = 12, CTR_IMPACTS = 13,
-       CTR_NEW = 14, CTR_SPAWN = 15, CTR_CLEAN = 16, CTR_COUNT = 17 };
+       CTR_NEW = 14, CTR_SPAWN = 15, CTR_CLEAN = 16, CTR_NCHUNK = 17, CTR_COUNT = 18 };
 enum { FS_RESID = 0, FS_COUNT = 4 };
 // ACC_SWEEP_PP / ACC_SWEEP_ST: sum over steps of sweeps x particle-pair /
 // static contacts (the solver's algorithmic work); ACC_STEPS: steps summed.

@@ -185,6 +185,24 @@ __device__ __forceinline__ void resid_terms(const Row &r, const Side &A, const S
   den += (double)__fadd_rn(l2, dot(lr, lr));
 }
 
+// Per-scene stop state of the solver (a bit per scene in shared memory).
+__device__ __forceinline__ bool scene_done(const uint32_t *done, uint32_t q) {
+  return (done[q >> 5] >> (q & 31u)) & 1u;
+}
+// The residual r of scene q at sweep it: CTA 0 keeps it as the scene's latest
+// (residual, sweeps); below the tolerance the scene is marked to stop, else it
+// competes for the largest residual of the scenes still sweeping (r >= 0, so
+// its bits order like the values).
+__device__ __forceinline__ void record_scene(const DevPtrs &d, uint32_t q, float r, float tol, uint32_t it,
+                                             uint32_t *done_new, uint32_t *rmax) {
+  if (blockIdx.x == 0) {
+    d.scene_res[q] = r;
+    d.scene_iters[q] = it;
+  }
+  if (tol > 0.f && r <= tol) atomicOr(done_new + (q >> 5), 1u << (q & 31u));
+  else atomicMax(rmax, __float_as_uint(r));
+}
+
 __device__ __forceinline__ void load_pair(const DevPtrs &d, const Row &r, Side &A, Side &B) {
   A = load_side(d, r.ab.x);
   if (r.dyn) B = load_side(d, r.ab.y);
@@ -223,8 +241,9 @@ constexpr int kShapes[][2] = {{768, 1}, {512, 2}, {640, 2}, {512, 3}};
 constexpr int kNumShapes = 4;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
-constexpr uint32_t kResChunk = 256;                  // residual: contacts per chunk of the colour order
-constexpr uint32_t kResSum = 512;                    // residual: threads adding up the chunks
+constexpr uint32_t kResSum = 512;                    // residual: threads adding up a scene's chunks
+constexpr uint32_t kWarpChunks = 1024;               // residual: scenes with at most this many chunks
+                                                     // are added by one warp, larger ones by the CTA
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
 //              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
 constexpr size_t kRowBytes = 72;
@@ -431,6 +450,9 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   __shared__ uint32_t s_mn[kPgsThreads / 32], s_mx[kPgsThreads / 32];
   __shared__ int s_flag, s_fail;
   __shared__ uint32_t s_waves, s_jlo, s_jhi;
+  __shared__ uint32_t s_done[TDS_MAX_SCENES / 32], s_done_new[TDS_MAX_SCENES / 32];
+  __shared__ uint32_t s_rmax, s_ndone, s_ndone_check;
+  __shared__ unsigned long long s_acc[2];
   const uint32_t ncol = min(d.ctr[CTR_NCOL], (uint32_t)TDS_MAX_COLOURS);
   const uint32_t nseg = 2 * ncol;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,7 +461,10 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
     s_waves = 0;
     s_fail = 0;
     s_jlo = s_jhi = blockIdx.x;
+    s_ndone = 0;
+    s_acc[0] = s_acc[1] = 0ull;
   }
+  for (uint32_t w = threadIdx.x; w < TDS_MAX_SCENES / 32; w += blockDim.x) s_done[w] = 0u;
   __syncthreads();
   for (uint32_t g = threadIdx.x; g < nseg; g += blockDim.x) seg_chunk(d, g, s_lo[g], s_hi[g]);
   __syncthreads();
@@ -571,6 +596,8 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         const WaveDesc q = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], w, kWave);
         Side A[kPerThread], B[kPerThread];
         uint32_t gp[kPerThread];  // colour-order index of each staged contact (or ~0)
+        uint32_t qs[kPerThread];  // its scene, once some scene of a batch has stopped
+        const bool skip_done = s_ndone != 0u;
         // gathers of every contact of this thread first (disjoint particles)
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
@@ -579,6 +606,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
           if (gp[j] != ~0u) {
             const uint2 ab = sab[li];
             if (ab.x != 0xFFFFFFFFu) {  // not a padding slot
+              if (skip_done) qs[j] = __ldcg(d.sid + ab.x);
               A[j] = load_side(d, ab.x);
               if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
               else B[j] = Side{f3(d.p_sv[gp[j]]), f3(d.p_sw[gp[j]]), 0.f, 0.f};
@@ -592,6 +620,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
             Row r;
             r.ab = sab[li];
             if (r.ab.x == 0xFFFFFFFFu) continue;
+            if (skip_done && scene_done(s_done, qs[j])) continue;  // its scene met the tolerance
             const float4 rn = srn[li], rq = srq[li];
             const float2 rm = srm[li];
             r.n = f3(rn); r.la = rn.w;
@@ -627,66 +656,109 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
     if (it == a.max_iters || (a.tol > 0.f && it == next_check)) {
       // the residual reads every contact: all colours of this sweep first
       if (a.sync && !grid_barrier(d.bar, d.err, gen, d.wait_ns)) { ok = false; break; }
-      // Summed in an order that no launch shape changes: the colour order in
-      // chunks of kResChunk contacts, each added by one warp (lane l takes
-      // l, l + 32, ..., then a fixed shuffle tree); then every CTA adds the
-      // chunk sums the same way (kResSum threads, fixed strides, fixed
-      // tree), so all CTAs take the same stop decision from the same value.
-      const uint32_t padded = d.ctr[CTR_PADDED];
-      const uint32_t nchunk = (padded + kResChunk - 1u) / kResChunk;
+      // Every scene has its own residual, summed in an order that neither the
+      // launch shape nor the other scenes of a batch change: its chunks (its
+      // contacts of one bucket, at most TDS_RES_CHUNK of them, consecutive in
+      // the colour order) are each added by one warp (lane l takes l, l + 32,
+      // ..., then a fixed shuffle tree); then every CTA adds each scene's
+      // chunk sums the same way, so all CTAs take the same stop decisions
+      // from the same values. A scene that met the tolerance stops sweeping
+      // and keeps the residual of that check.
+      const uint32_t nchunk = d.ctr[CTR_NCHUNK];
       const uint32_t lane = threadIdx.x & 31u;
       for (uint32_t ch = tid >> 5; ch < nchunk; ch += stride >> 5) {
-        double cn = 0.0, cd = 0.0;
-        for (uint32_t q = 0; q < kResChunk; q += 32u) {
-          const uint32_t p = ch * kResChunk + q + lane;
-          if (p >= padded || __ldcg(&d.p_ab[p].x) == 0xFFFFFFFFu) continue;  // padding slot
+        const uint4 cd = __ldcg(d.chunk + ch);
+        if (scene_done(s_done, cd.z)) continue;
+        double cn = 0.0, cdn = 0.0;
+        for (uint32_t q = lane; q < cd.y; q += 32u) {
+          const uint32_t p = cd.x + q;
           Row r = load_row(d, p);
           Side A, B;
           load_pair(d, r, A, B);
-          resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, cn, cd);
+          resid_terms(r, A, B, __ldcg(d.p_la + p), __ldcg(d.p_lb + p), a.sig_t, a.sig_r, cn, cdn);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           cn += __shfl_down_sync(0xffffffffu, cn, o);
-          cd += __shfl_down_sync(0xffffffffu, cd, o);
+          cdn += __shfl_down_sync(0xffffffffu, cdn, o);
         }
         if (lane == 0) {
           __stcg(d.dres + 2 * ch, cn);
-          __stcg(d.dres + 2 * ch + 1, cd);
+          __stcg(d.dres + 2 * ch + 1, cdn);
         }
       }
       if (!grid_barrier(d.bar, d.err, gen, d.wait_ns)) { ok = false; break; }
-      if (threadIdx.x < kResSum) {
-        double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
-        uint32_t ch = threadIdx.x;
-        for (; ch + kResSum < nchunk; ch += 2u * kResSum) {
-          const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
-          const double2 v = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch + kResSum);
-          n0 += u.x; d0 += u.y;
-          n1 += v.x; d1 += v.y;
-        }
-        if (ch < nchunk) {
-          const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
-          n0 += u.x; d0 += u.y;
-        }
-        s_rn[threadIdx.x] = n0 + n1;
-        s_rd[threadIdx.x] = d0 + d1;
-      }
+      const uint32_t S = d.nscenes;
+      for (uint32_t w = threadIdx.x; w < (S + 31u) / 32u; w += blockDim.x) s_done_new[w] = 0u;
+      if (threadIdx.x == 0) s_rmax = 0u;
       __syncthreads();
-      for (uint32_t h = kResSum / 2u; h > 0u; h >>= 1) {
-        if (threadIdx.x < h) {
-          s_rn[threadIdx.x] += s_rn[threadIdx.x + h];
-          s_rd[threadIdx.x] += s_rd[threadIdx.x + h];
+      // scenes with many chunks: the whole CTA adds them (fixed strides, fixed tree)
+      for (uint32_t q = 0; q < S; ++q) {
+        const uint32_t c0 = __ldcg(d.scq_chunk + (size_t)q * TDS_NBUCKETS);
+        const uint32_t c1 = __ldcg(d.scq_chunk + (size_t)(q + 1) * TDS_NBUCKETS);
+        if (c1 - c0 <= kWarpChunks || scene_done(s_done, q)) continue;
+        if (threadIdx.x < kResSum) {
+          double n0 = 0.0, n1 = 0.0, d0 = 0.0, d1 = 0.0;
+          uint32_t ch = c0 + threadIdx.x;
+          for (; ch + kResSum < c1; ch += 2u * kResSum) {
+            const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
+            const double2 v = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch + kResSum);
+            n0 += u.x; d0 += u.y;
+            n1 += v.x; d1 += v.y;
+          }
+          if (ch < c1) {
+            const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
+            n0 += u.x; d0 += u.y;
+          }
+          s_rn[threadIdx.x] = n0 + n1;
+          s_rd[threadIdx.x] = d0 + d1;
         }
         __syncthreads();
+        for (uint32_t h = kResSum / 2u; h > 0u; h >>= 1) {
+          if (threadIdx.x < h) {
+            s_rn[threadIdx.x] += s_rn[threadIdx.x + h];
+            s_rd[threadIdx.x] += s_rd[threadIdx.x + h];
+          }
+          __syncthreads();
+        }
+        if (threadIdx.x == 0)
+          record_scene(d, q, (float)(sqrt(s_rn[0]) / fmax(sqrt(s_rd[0]), 1e-12)), a.tol, it, s_done_new, &s_rmax);
+        __syncthreads();
       }
+      // the other scenes: one warp each (lane strides, fixed shuffle tree)
+      for (uint32_t q = threadIdx.x >> 5; q < S; q += blockDim.x >> 5) {
+        const uint32_t c0 = __ldcg(d.scq_chunk + (size_t)q * TDS_NBUCKETS);
+        const uint32_t c1 = __ldcg(d.scq_chunk + (size_t)(q + 1) * TDS_NBUCKETS);
+        if (c1 - c0 > kWarpChunks || scene_done(s_done, q)) continue;
+        double tn = 0.0, td = 0.0;
+        for (uint32_t ch = c0 + lane; ch < c1; ch += 32u) {
+          const double2 u = __ldcg(reinterpret_cast<const double2 *>(d.dres) + ch);
+          tn += u.x;
+          td += u.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          tn += __shfl_down_sync(0xffffffffu, tn, o);
+          td += __shfl_down_sync(0xffffffffu, td, o);
+        }
+        if (lane == 0) record_scene(d, q, (float)(sqrt(tn) / fmax(sqrt(td), 1e-12)), a.tol, it, s_done_new, &s_rmax);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_ndone_check = 0u;
+      __syncthreads();
+      for (uint32_t w = threadIdx.x; w < (S + 31u) / 32u; w += blockDim.x) {
+        s_done[w] |= s_done_new[w];
+        atomicAdd(&s_ndone_check, (uint32_t)__popc(s_done[w]));
+      }
+      __syncthreads();
       if (threadIdx.x == 0) {
-        const double tn = s_rn[0], td = s_rd[0];
-        resid = (float)(sqrt(tn) / fmax(sqrt(td), 1e-12));
-        s_flag = a.tol > 0.f && resid <= a.tol;
+        s_ndone = s_ndone_check;
+        // the largest residual of the scenes still sweeping (0 when all stopped)
+        resid = __uint_as_float(s_rmax);
+        s_flag = a.tol > 0.f && s_ndone == S;
         // next check: a fixed period, or the sweep where the geometric decay
-        // measured between the last two checks reaches the tolerance (at
-        // least 2 and at most 64 sweeps on); every CTA computes the same
+        // of that residual between the last two checks reaches the tolerance
+        // (at least 2 and at most 64 sweeps on); every CTA computes the same
         // value from the same residuals
         uint32_t gap = a.every;
         if (a.every == 0) {
@@ -711,16 +783,42 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
   if (threadIdx.x == 0)
     for (uint32_t q = consumed; q < issued; ++q)
       if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err, TDS_BARRIER_NS)) break;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint32_t nc = d.ctr[CTR_NC];
-    d.ctr[CTR_ITERS] = it;
-    d.fscal[FS_RESID] = resid;
-    uint32_t nst = 0;
-    for (uint32_t c = 0; c < ncol; ++c) nst += d.bend[2 * c + 1] - d.bstart[2 * c + 1];
-    d.acc[ACC_SWEEP_PP] += (unsigned long long)it * (nc - nst);
-    d.acc[ACC_SWEEP_ST] += (unsigned long long)it * nst;
-    d.acc[ACC_CONTACTS] += nc;
-    d.acc[ACC_STEPS] += 1;
+  const bool all_ok = __syncthreads_and(ok) != 0;  // every thread of the CTA reaches this point
+  if (blockIdx.x == 0 && all_ok) {
+    // statistics: the sweeps done (the most any scene did), the largest final
+    // residual, and per scene its sweeps x its contacts (the solver's work)
+    __syncthreads();
+    const uint32_t S = d.nscenes;
+    if (it == 0u)
+      for (uint32_t q = threadIdx.x; q < S; q += blockDim.x) {
+        d.scene_iters[q] = 0u;
+        d.scene_res[q] = -1.f;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) s_rmax = 0u;
+    __syncthreads();
+    unsigned long long pp = 0ull, sc = 0ull;
+    for (uint32_t q = threadIdx.x; q < S; q += blockDim.x) {
+      const unsigned long long iq = d.scene_iters[q];
+      for (uint32_t b = 0; b < TDS_NBUCKETS; ++b) {
+        const unsigned long long c = d.scq_cnt[(size_t)q * TDS_NBUCKETS + b];
+        if (b & 1u) sc += iq * c;
+        else pp += iq * c;
+      }
+      const float r = d.scene_res[q];
+      if (r > 0.f) atomicMax(&s_rmax, __float_as_uint(r));
+    }
+    if (pp) atomicAdd(&s_acc[0], pp);
+    if (sc) atomicAdd(&s_acc[1], sc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      d.ctr[CTR_ITERS] = it;
+      d.fscal[FS_RESID] = it == 0u ? -1.f : __uint_as_float(s_rmax);
+      d.acc[ACC_SWEEP_PP] += s_acc[0];
+      d.acc[ACC_SWEEP_ST] += s_acc[1];
+      d.acc[ACC_CONTACTS] += d.ctr[CTR_NC];
+      d.acc[ACC_STEPS] += 1;
+    }
   }
 }
 

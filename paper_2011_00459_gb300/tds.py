@@ -34,7 +34,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
             "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid",
             "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii",
-            "tds_state_bytes", "tds_save_state", "tds_load_state"]
+            "tds_state_bytes", "tds_save_state", "tds_load_state", "tds_batch_read_solve"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes compiled (threads, contacts per thread)
@@ -190,6 +190,7 @@ def lib() -> ctypes.CDLL:
         L.tds_batch_set_tool_pose.argtypes = [vp, ctypes.c_uint32, _fp, _fp, _fp, _fp]
         L.tds_batch_read_particles.argtypes = [vp, ctypes.c_uint32] + [vp] * 9 + [ctypes.c_uint32]
         L.tds_batch_read_tool_forces.argtypes = [vp, vp, ctypes.c_uint32]
+        L.tds_batch_read_solve.argtypes = [vp, vp, vp, ctypes.c_uint32]
         L.tds_set_graph.argtypes = [vp, ctypes.c_int32]
         L.tds_batch_set_tool_poses.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_aggregate_bodies.argtypes = [vp, ctypes.POINTER(Zone), ctypes.c_uint32, ctypes.POINTER(Aggregate)]
@@ -587,6 +588,15 @@ class Batch(Scene):
         out = np.zeros((len(self.sizes), 6), np.float32)
         _check(lib().tds_batch_read_tool_forces(self.h, ctypes.c_void_p(out.ctypes.data), len(self.sizes)))
         return out.astype(np.float64)
+
+    def read_solve(self) -> dict:
+        """Each scene's solve in the last step: residual (float32) at its last
+        check and sweeps (uint32)."""
+        res = np.zeros(len(self.sizes), np.float32)
+        sw = np.zeros(len(self.sizes), np.uint32)
+        _check(lib().tds_batch_read_solve(self.h, ctypes.c_void_p(res.ctypes.data), ctypes.c_void_p(sw.ctypes.data),
+                                          len(self.sizes)))
+        return {"residual": res, "sweeps": sw}
 
 
 # ---------------------------------------------------------------------------

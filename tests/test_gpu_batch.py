@@ -278,3 +278,50 @@ def test_autotuner_picks_a_candidate_and_caches_it(tds, tmp_path):
     again = autotune.tune(sim, path=path)
     assert again["source"] == "cache" and again["shape"] == r["shape"]
     sim.g.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_every_bed_stops_at_its_own_residual(tds, graph):
+    """In residual mode each bed of a batch has its own residual and stops
+    sweeping at the first check where it is below the tolerance, exactly as
+    when stepped alone: per bed the same sweeps, the same residual (<= tol)
+    and the same state, bit for bit, over several steps with moving tools."""
+    import torch
+
+    tol, every, steps = 1e-4, 5, 3
+    scenes = [packed_scene(900, 41, mu_t=0.5, mu_r=0.1, iters=3000, tol=tol),
+              packed_scene(1900, 42, mu_t=0.7, mu_r=0.2, iters=3000, tol=tol),
+              packed_scene(400, 43, mu_t=0.9, mu_r=0.0, iters=3000, tol=tol),
+              packed_scene(1200, 44, cohesion=0.0, mu_t=0.4, iters=3000, tol=tol)]
+    b = tds.Batch(scenes, stream=torch.cuda.Stream())
+    b.set_graph(graph)
+    b.set_solver(3000, tol, every)
+    per_step = []
+    for k in range(steps):
+        b.set_tool_poses([moved(s["tool"], k) for s in scenes])
+        b.step(1)
+        per_step.append(b.read_solve())
+    st = b.stats()
+    for q, sc in enumerate(scenes):
+        g = tds.Scene(sc, stream=torch.cuda.Stream())
+        g.set_graph(graph)
+        g.set_solver(3000, tol, every)
+        for k in range(steps):
+            g.set_tool_pose(moved(sc["tool"], k))
+            g.step(1)
+            alone = g.stats()
+            got = per_step[k]
+            assert got["sweeps"][q] == alone["iterations"], (q, k)
+            assert got["residual"][q] == np.float32(alone["residual"]), (q, k)
+            assert got["residual"][q] <= tol and got["sweeps"][q] < 3000, (q, k)
+        a = g.read_particles()
+        g.close()
+        mine = b.read_scene(q)
+        for key in ("x", "v", "w"):
+            assert np.array_equal(mine[key], a[key]), (q, key)
+    sweeps = np.stack([p["sweeps"] for p in per_step])
+    print("sweeps per bed and step:", sweeps.tolist())
+    assert len(set(sweeps[-1].tolist())) > 1  # the beds do stop at different sweeps
+    assert st["iterations"] == sweeps[-1].max()
+    assert st["residual"] == per_step[-1]["residual"].max()
+    b.close()

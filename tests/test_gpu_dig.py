@@ -4,15 +4,16 @@ wide at 0.5 m/s, 0.1 m deep, 50 sweeps per step).
 
 A push through a granular bed is chaotic: two FP64 oracle runs whose initial
 positions differ by 1e-7 m end in different microstates: over perturbed runs
-the median tool force over the push has a standard deviation of 8 %, the
-mass of particles moved by more than one mean radius 2.7 %, the mass-weighted
-displacement of the soil along the push 1.7 %. The FP32 GPU path is such a
-perturbation of every step. So the two sides are compared as ensembles:
-32 copies of one oracle-settled bed with seeded 1e-7 m perturbations, run on
-the GPU as one batch and by the oracle one by one. Their means must agree
-within 2 % for the displaced soil (sum of m dx along the push) and, for the
-median force and the moved mass, within three standard errors of the
-difference of two such means: 6 % and 3 %."""
+the median tool force over the push has a standard deviation of about 8 %,
+the mass of particles moved by more than one mean radius 2.7 %, the
+mass-weighted displacement of the soil along the push 1.7 %. The FP32 GPU
+path is such a perturbation of every step. So the two sides are compared as
+ensembles: copies of one oracle-settled bed with seeded 1e-7 m
+perturbations, run on the GPU as one batch and by the oracle in parallel
+workers. With 384 members per side, three standard errors of the difference
+of the two means stay below 2 % even for the force; the means must agree
+within 2 % for all three quantities (tool force, displaced soil, moved mass).
+The measured differences and standard errors are printed."""
 import multiprocessing as mp
 
 import numpy as np
@@ -22,7 +23,7 @@ from paper_2011_00459_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
 
-MEMBERS = 32
+MEMBERS = 384
 STEPS = 60
 SEED = 3
 
@@ -84,7 +85,7 @@ def test_dig_force_and_displaced_soil_match_the_oracle_ensemble(tds):
     scene = S.small(seed=SEED)
     path = S.tool_path(scene, surface)
     with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
-        ref = np.array(pool.map(oracle_member, [(k, x, v, w, surface) for k in range(MEMBERS)]))
+        ref = np.array(pool.map(oracle_member, [(k, x, v, w, surface) for k in range(MEMBERS)], chunksize=4))
     beds = [dict(scene, x=member_x(x, k).astype(np.float32), v=v.astype(np.float32), w=w.astype(np.float32))
             for k in range(MEMBERS)]
     b = tds.Batch(beds)
@@ -96,7 +97,14 @@ def test_dig_force_and_displaced_soil_match_the_oracle_ensemble(tds):
     gpu = np.array([aggregates(scene, x, b.read_scene(k)["x"], fx[:, k]) for k in range(MEMBERS)])
     b.close()
     g, r = gpu.mean(0), ref.mean(0)
+    se = np.sqrt(gpu.var(0, ddof=1) / MEMBERS + ref.var(0, ddof=1) / MEMBERS) / np.abs(r)
+    rel = g / r - 1.0
+    for q, name in enumerate(("median tool force", "displaced soil (sum m dx)", "moved mass")):
+        print(f"{name}: gpu {g[q]:.6g} oracle {r[q]:.6g} difference {100 * rel[q]:+.2f} % "
+              f"(standard error of the difference {100 * se[q]:.2f} %, member spread "
+              f"{100 * ref[:, q].std(ddof=1) / abs(r[q]):.1f} %)")
     assert r[0] < 0.0 and r[1] > 0.0  # the soil resists the push and moves with it
-    assert abs(g[1] / r[1] - 1.0) <= 0.02, (g, r)  # displaced soil, sum m dx
-    assert abs(g[0] / r[0] - 1.0) <= 0.06, (g, r)  # median tool force
-    assert abs(g[2] / r[2] - 1.0) <= 0.03, (g, r)  # mass moved more than one mean radius
+    assert np.all(3.0 * se <= 0.02), se  # the ensembles resolve the 2 % bar
+    assert abs(rel[0]) <= 0.02, (g, r)  # median tool force
+    assert abs(rel[1]) <= 0.02, (g, r)  # displaced soil, sum m dx
+    assert abs(rel[2]) <= 0.02, (g, r)  # mass moved more than one mean radius
