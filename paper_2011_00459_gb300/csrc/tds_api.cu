@@ -678,6 +678,9 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
   if (ce == cudaSuccess) ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_col, tds_colour_kernel(), 256, 0);
   if (ce != cudaSuccess || occ_pgs < 1 || occ_col < 1) {
     delete s;
+    if (ce == cudaSuccess)
+      return fail(TDS_ERR_CUDA, "a solver or colouring CTA shape does not fit on one SM (shared memory or "
+                                "registers)");
     return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
   }
   s->pgs_blocks = pgs_blocks_for(s->L.n, sms);  // one co-resident CTA per SM at most

@@ -241,7 +241,7 @@ constexpr int kShapes[][2] = {{768, 1}, {512, 2}, {640, 2}, {512, 3}};
 constexpr int kNumShapes = 4;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
-constexpr uint32_t kResSum = 512;                    // residual: threads adding up a scene's chunks
+constexpr uint32_t kResSum = 256;                    // residual: threads adding up a large scene's chunks
 constexpr uint32_t kWarpChunks = 1024;               // residual: scenes with at most this many chunks
                                                      // are added by one warp, larger ones by the CTA
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
