@@ -636,6 +636,14 @@ def run_tds(args, rank: int, world: int, local_rank: int):
             fields = time_fields(g, work, stream, args.steps, tds)
         one = g.scenes[0] if isinstance(g, SceneGroup) else g
         launch_cfg = one.launch_config()
+        if isinstance(work, list) and not isinstance(g, SceneGroup):
+            sv = g.read_solve()  # each bed's own solve in the last timed step
+            r, k = sv["residual"].astype(np.float64), sv["sweeps"].astype(np.int64)
+            launch_cfg["per_bed"] = {
+                "beds": int(len(r)), "max_final_residual": float(r.max()),
+                "beds_above_tol": int((r > first.get("tol", 0.0)).sum()) if first.get("tol", 0) > 0 else None,
+                "beds_at_sweep_cap": int((k >= int(first["iters"])).sum()),
+                "sweeps_min_median_max": [int(k.min()), float(np.median(k)), int(k.max())]}
         if tuned:
             launch_cfg["autotune"] = {k: tuned[k] for k in ("source", "ms", "default_ms", "steps") if k in tuned}
         g.close()
@@ -738,11 +746,13 @@ def oracle_sample(scene: dict, seconds: float, seed: int, steps: int | None = No
 
 
 def cpu_baseline(scene: dict, seconds: float, seed: int, warmup: int, gpu_sweeps: float | None) -> dict:
-    """The oracle on all host cores (the reported baseline) and on one thread,
-    with the CPU model, the oracle's sweeps per step and the GPU's."""
+    """The oracle on one thread for about ``seconds``, then on all host cores
+    (the reported baseline) over exactly the same steps from the same state
+    (the same results bit for bit, so the same sweeps), with the CPU model,
+    the oracle's sweeps per step and the GPU's."""
     cores = os.cpu_count() or 1
-    val, desc, _, sw = oracle_sample(scene, seconds, seed, warmup=warmup, threads=cores)
-    v1, d1, _, sw1 = oracle_sample(scene, seconds, seed, warmup=warmup, threads=1)
+    v1, d1, k, sw1 = oracle_sample(scene, seconds, seed, warmup=warmup, threads=1)
+    val, desc, _, sw = oracle_sample(scene, 0.0, seed, steps=k, warmup=warmup, threads=cores)
     return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
             "sweeps_per_step": sw, "gpu_sweeps_per_step": gpu_sweeps, "cpu_model": cpu_model(),
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": d1, "sweeps_per_step": sw1}}
@@ -843,10 +853,12 @@ def batched_form(args, rank: int, world: int, local_rank: int) -> tuple:
     residual, timed like the headline; also returns its launch shape."""
     a = batched_args(args)
     work, n_all, ms, st, launches, clk, e2e, fixed, launch_cfg = run_tds(a, rank, world, local_rank)
+    beds = launch_cfg.pop("per_bed", None)
     return ({"workload": describe(work, a)["workload"], "value": n_all * a.steps / (ms * 1e-3), "unit": UNIT,
              "ms_per_step": ms / a.steps, "warm_start": "previous step",
              "mean_sweeps": (st["sweep_contacts_pp"] + st["sweep_contacts_static"]) / max(1, st["sum_contacts"]),
-             "final_residual": st["residual"], "gpu_launches": int(launches)}, launch_cfg)
+             "final_residual": st["residual"], "per_bed_last_step": beds, "gpu_launches": int(launches)},
+            launch_cfg)
 
 
 def unbatched_form(args, rank: int, world: int, local_rank: int, steps: int = 3) -> dict:
