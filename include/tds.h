@@ -427,8 +427,8 @@ tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
  * with the CTAs whose particles it can touch (1, the default) or all CTAs
  * with a grid barrier (0); colour_blocks: persistent colouring CTAs;
  * pgs_threads x pgs_per_thread: the solver CTA's threads and contacts per
- * thread, one of the compiled shapes 768x1 (the default) and 512x2 (both 0
- * keep the current shape).
+ * thread, one of the compiled shapes 768x1 (the default), 512x2, 640x2,
+ * 512x3 (both 0 keep the current shape).
  * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
  * wait_limit_us: how long [microseconds] any CTA of the step's persistent
  * kernels waits for other CTAs (a grid barrier, a neighbour's progress flag)

@@ -65,7 +65,7 @@ def store_cache(key: str, entry: dict, path: str | None = None) -> None:
 
 
 SYNC_MODES = (1, 0)  # neighbour synchronisation, grid barrier
-SHAPES = ((768, 1), (512, 2))  # solver CTA shapes the library compiles
+SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes the library compiles
 KEYS = ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads", "pgs_per_thread")
 
 

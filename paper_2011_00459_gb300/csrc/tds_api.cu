@@ -386,7 +386,6 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.c_key = c.take<unsigned long long>(cap);
   d.c_rn = c.take<float4>(cap); d.c_rq = c.take<float4>(cap);
   d.c_rm = c.take<float2>(cap);
-  d.c_rd = c.take<float4>(cap);
   d.c_sv = c.take<float4>(cap); d.c_sw = c.take<float4>(cap);
   d.c_la = c.take<float4>(cap); d.c_lb = c.take<float2>(cap);
   d.inc_cnt = c.take<uint32_t>(n + 1); d.inc_start = c.take<uint32_t>(n + 1);
@@ -406,7 +405,6 @@ size_t carve(Carver &c, const Layout &L, DevPtrs &d, Extra &x, int pgs_blocks) {
   d.p_ab = c.take<uint2>(pc);
   d.p_rn = c.take<float4>(pc); d.p_rq = c.take<float4>(pc);
   d.p_rm = c.take<float2>(pc);
-  d.p_rd = c.take<float4>(pc);
   d.p_sv = c.take<float4>(pc); d.p_sw = c.take<float4>(pc);
   d.p_la = c.take<float4>(pc); d.p_lb = c.take<float2>(pc);
   d.p_il = c.take<float4>(pc); d.p_il2 = c.take<float4>(pc);

@@ -248,7 +248,6 @@ __global__ void __launch_bounds__(256) k_bucket_scatter(DevPtrs d) {
       d.p_rn[p] = d.c_rn[c];
       d.p_rq[p] = d.c_rq[c];
       d.p_rm[p] = d.c_rm[c];
-      d.p_rd[p] = d.c_rd[c];
       if (bk & 1u) { d.p_sv[p] = d.c_sv[c]; d.p_sw[p] = d.c_sw[c]; }
       d.p_la[p] = d.c_la[c];
       d.p_lb[p] = d.c_lb[c];

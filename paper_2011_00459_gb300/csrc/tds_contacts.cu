@@ -216,7 +216,6 @@ struct Writer {
   const StepConsts &k;
   uint32_t i, me, next;
   float4 P, Va;
-  float iIa;  // 1/I of particle a
   int use_prev;
   uint32_t pf, pc;
 
@@ -225,7 +224,7 @@ struct Writer {
   // side's velocity at the start of the step.
   __device__ void emit(const SceneGeo &G, uint32_t b_slot, uint32_t other, float3 n, float delta,
                        float rb, float dstar, float estar, float rbar, float dfloor, bool is_static,
-                       bool is_tool, float3 vb, float3 vs, float3 ws, float imb, float iIb) {
+                       bool is_tool, float3 vb, float3 vs, float3 ws) {
     uint32_t c = next++;
     if (c >= k.cap) return;
     const float h = k.dt;
@@ -251,19 +250,6 @@ struct Writer {
     d.c_rn[c] = make_float4(n.x, n.y, n.z, la);
     d.c_rq[c] = make_float4(lb, qn, Sn, fc);
     d.c_rm[c] = make_float2(mu, rmu);
-    // Constant during the step: the inverse diagonal entries of the normal,
-    // tangent and rolling row groups, 1/(1/m_a + 1/m_b + Sigma_n),
-    // 1/(1/m_a + 1/m_b + la^2/I_a + lb^2/I_b + sigma_t), 1/(1/I_a + 1/I_b +
-    // sigma_r), and the reciprocal in the tangent basis of the normal. The
-    // solver's sweeps read them instead of recomputing them, written with the
-    // same roundings as the solver's own formulas.
-    {
-      const float imab = __fadd_rn(Va.w, imb);
-      const float rot = __fmaf_rn(__fmul_rn(lb, lb), iIb, __fmul_rn(__fmul_rn(la, la), iIa));
-      d.c_rd[c] = make_float4(__frcp_rn(__fadd_rn(imab, Sn)), __frcp_rn(__fadd_rn(__fadd_rn(imab, rot), k.sig_t)),
-                              __frcp_rn(__fadd_rn(__fadd_rn(iIa, iIb), k.sig_r)),
-                              -__frcp_rn(__fadd_rn(copysignf(1.0f, n.z), n.z)));
-    }
     if (is_static) {
       d.c_sv[c] = make_float4(vs.x, vs.y, vs.z, 0.0f);
       d.c_sw[c] = make_float4(ws.x, ws.y, ws.z, 0.0f);
@@ -306,10 +292,9 @@ struct Writer {
     float rs = P.w + Q.w;
     float dstar = 2.0f * P.w * Q.w / rs;
     float4 Vb = d.pv[2 * j];
-    const float iIb = d.pv[2 * j + 1].w;
     float3 z3 = make_float3(0.f, 0.f, 0.f);
     emit(k.geo[d.sid[i]], j, pj, n, delta, Q.w, dstar, k.estar_pair, dstar, 1e-5f * rs, false, false,
-         f3(Vb), z3, z3, Vb.w, iIb);
+         f3(Vb), z3, z3);
   }
 
   __device__ void surface(const SceneGeo &G, uint32_t surf, float3 ns, float s, bool is_tool) {
@@ -324,7 +309,7 @@ struct Writer {
       vs = make_float3(G.tv[0], G.tv[1], G.tv[2]) + cross(ws, rel);
     }
     emit(G, TDS_STATIC | surf, TDS_STATIC | surf, n, delta, 0.f, 2.0f * P.w, k.estar_static, P.w,
-         2e-5f * P.w, true, is_tool, vs, vs, ws, 0.f, 0.f);
+         2e-5f * P.w, true, is_tool, vs, vs, ws);
   }
 
   __device__ void hf(const SceneGeo &G, const HfHit &hit) {
@@ -360,7 +345,7 @@ struct Writer {
 
 __global__ void k_write(DevPtrs d, StepConsts k, int use_prev) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
-    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.pv[2 * i], d.pv[2 * i + 1].w, use_prev, 0u, 0u};
+    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.pv[2 * i], use_prev, 0u, 0u};
     if (use_prev) {
       w.pf = d.prev_first[0][w.me];
       w.pc = d.prev_cnt[0][w.me];

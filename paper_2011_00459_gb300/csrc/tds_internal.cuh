@@ -112,7 +112,6 @@ struct DevPtrs {
   unsigned long long *c_key;
   float4 *c_rn, *c_rq;        // (n, la), (lb, q_n, Sigma_n, f_c)
   float2 *c_rm;               // (mu, rbar mu_r)
-  float4 *c_rd;               // (1/D_n, 1/D_t, 1/D_r, tangent-basis reciprocal), constant in a step
   float4 *c_sv, *c_sw;        // static side: point velocity, spin
   float4 *c_la;               // initial impulses (n, t1, t2, r.x)
   float2 *c_lb;               // (r.y, r.z)
@@ -131,7 +130,6 @@ struct DevPtrs {
   uint2 *p_ab;
   float4 *p_rn, *p_rq;
   float2 *p_rm;
-  float4 *p_rd;
   float4 *p_sv, *p_sw;
   float4 *p_la;
   float2 *p_lb;
@@ -237,15 +235,12 @@ __device__ __forceinline__ float3 cross(float3 a, float3 b) {
 // Christensen, Hery, Kensler, Liani, Villemin, "Building an Orthonormal
 // Basis, Revisited", JCGT 6(1), 2017). The 2-D tangent update is invariant
 // under the choice of basis, since its effective mass is isotropic.
-// onb_pre takes the basis' reciprocal a = -1/(sign(n_z) + n_z) precomputed.
-__device__ __forceinline__ void onb_pre(float3 n, float a, float3 &t1, float3 &t2) {
+__device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
   const float sgn = copysignf(1.0f, n.z);
+  const float a = -__frcp_rn(__fadd_rn(sgn, n.z));
   const float b = __fmul_rn(__fmul_rn(n.x, n.y), a);
   t1 = make_float3(__fmaf_rn(__fmul_rn(sgn, __fmul_rn(n.x, n.x)), a, 1.0f), __fmul_rn(sgn, b), -__fmul_rn(sgn, n.x));
   t2 = make_float3(b, __fmaf_rn(__fmul_rn(n.y, n.y), a, sgn), -n.y);
-}
-__device__ __forceinline__ void onb(float3 n, float3 &t1, float3 &t2) {
-  onb_pre(n, -__frcp_rn(__fadd_rn(copysignf(1.0f, n.z), n.z)), t1, t2);
 }
 
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014): the colouring

@@ -52,7 +52,6 @@ struct Row {
   uint2 ab;
   float3 n;
   float la, lb, qn, Sn, fc, mu, rmu;
-  float iDn, iDt, iDr, ob;  // inverse diagonals, tangent-basis reciprocal
   float3 sv, sw;
   bool dyn;
 };
@@ -66,8 +65,6 @@ __device__ __forceinline__ Row load_row(const DevPtrs &d, uint32_t p) {
   r.la = rn.w;
   r.lb = rq.x; r.qn = rq.y; r.Sn = rq.z; r.fc = rq.w;
   r.mu = rm.x; r.rmu = rm.y;
-  const float4 rd = d.p_rd[p];
-  r.iDn = rd.x; r.iDt = rd.y; r.iDr = rd.z; r.ob = rd.w;
   r.dyn = is_dyn(r.ab.y);
   if (!r.dyn) { r.sv = f3(d.p_sv[p]); r.sw = f3(d.p_sw[p]); }
   return r;
@@ -121,27 +118,32 @@ __device__ __forceinline__ float3 slip(const Row &r, const Side &A, const Side &
   return (B.v - A.v) - cross(axpy(r.la, A.w, r.lb * B.w), r.n);
 }
 
-// Diagonal entry of the normal row: 1/m_a + 1/m_b + Sigma_n. The inverse
-// diagonals of the step's rows come with the rows (written by the
-// narrowphase with these roundings); the impact stage, whose rows have no
-// compliance, takes its own normal entry.
+// Diagonal entries of the three row groups: 1/m_a + 1/m_b + Sigma_n,
+// 1/m_a + 1/m_b + la^2/I_a + lb^2/I_b + sigma_t, 1/I_a + 1/I_b + sigma_r.
 __device__ __forceinline__ float diag_n(const Row &r, const Side &A, const Side &B) {
   return __fadd_rn(__fadd_rn(A.im, B.im), r.Sn);
+}
+__device__ __forceinline__ float diag_t(const Row &r, const Side &A, const Side &B, float sig_t) {
+  const float rot = __fmaf_rn(__fmul_rn(r.lb, r.lb), B.iI, __fmul_rn(__fmul_rn(r.la, r.la), A.iI));
+  return __fadd_rn(__fadd_rn(__fadd_rn(A.im, B.im), rot), sig_t);
+}
+__device__ __forceinline__ float diag_r(const Side &A, const Side &B, float sig_r) {
+  return __fadd_rn(__fadd_rn(A.iI, B.iI), sig_r);
 }
 
 // One projected Gauss-Seidel update of one contact.
 __device__ __forceinline__ void pgs_update(const Row &r, Side &A, Side &B, float4 &L0, float2 &L1,
                                            float sig_t, float sig_r) {
   // normal row
-  const float iDn = r.iDn;
+  const float iDn = __frcp_rn(diag_n(r, A, B));
   const float res = __fsub_rn(__fmaf_rn(r.Sn, L0.x, dot(r.n, B.v - A.v)), r.qn);
   const float ln = fmaxf(__fmaf_rn(-res, iDn, L0.x), -r.fc);
   apply_normal(r, A, B, __fsub_rn(ln, L0.x));
   L0.x = ln;
   // tangent rows (Coulomb disk)
   float3 t1, t2;
-  onb_pre(r.n, r.ob, t1, t2);
-  const float iDt = r.iDt;
+  onb(r.n, t1, t2);
+  const float iDt = __frcp_rn(diag_t(r, A, B, sig_t));
   const float3 u = slip(r, A, B);
   float y1 = __fmaf_rn(-__fmaf_rn(sig_t, L0.y, dot(t1, u)), iDt, L0.y);
   float y2 = __fmaf_rn(-__fmaf_rn(sig_t, L0.z, dot(t2, u)), iDt, L0.z);
@@ -150,7 +152,7 @@ __device__ __forceinline__ void pgs_update(const Row &r, Side &A, Side &B, float
   L0.y = y1;
   L0.z = y2;
   // rolling rows (ball)
-  const float iDr = r.iDr;
+  const float iDr = __frcp_rn(diag_r(A, B, sig_r));
   const float3 lr = make_float3(L0.w, L1.x, L1.y);
   float3 y = axpy(-iDr, axpy(sig_r, lr, B.w - A.w), lr);
   ball(y, __fmul_rn(r.rmu, fabsf(ln)));
@@ -165,16 +167,16 @@ __device__ __forceinline__ void resid_terms(const Row &r, const Side &A, const S
                                             float2 L1, float sig_t, float sig_r, double &num,
                                             double &den) {
   const float wn = __fsub_rn(__fmaf_rn(r.Sn, L0.x, dot(r.n, B.v - A.v)), r.qn);
-  const float pn = fmaxf(__fmaf_rn(-wn, r.iDn, L0.x), -r.fc);
+  const float pn = fmaxf(__fmaf_rn(-wn, __frcp_rn(diag_n(r, A, B)), L0.x), -r.fc);
   float3 t1, t2;
-  onb_pre(r.n, r.ob, t1, t2);
-  const float iDt = r.iDt;
+  onb(r.n, t1, t2);
+  const float iDt = __frcp_rn(diag_t(r, A, B, sig_t));
   const float3 u = slip(r, A, B);
   float y1 = __fmaf_rn(-__fmaf_rn(sig_t, L0.y, dot(t1, u)), iDt, L0.y);
   float y2 = __fmaf_rn(-__fmaf_rn(sig_t, L0.z, dot(t2, u)), iDt, L0.z);
   disk(y1, y2, __fmul_rn(r.mu, fabsf(L0.x)));
   const float3 lr = make_float3(L0.w, L1.x, L1.y);
-  float3 y = axpy(-r.iDr, axpy(sig_r, lr, B.w - A.w), lr);
+  float3 y = axpy(-__frcp_rn(diag_r(A, B, sig_r)), axpy(sig_r, lr, B.w - A.w), lr);
   ball(y, __fmul_rn(r.rmu, fabsf(L0.x)));
   const float e0 = __fsub_rn(L0.x, pn), e1 = __fsub_rn(L0.y, y1), e2 = __fsub_rn(L0.z, y2);
   const float3 e3 = lr - y;
@@ -235,26 +237,19 @@ struct SolveArgs {
 // 1M bed and the batch, one contact per thread over 768 threads is fastest:
 // each colour phase is a latency chain, and a thread's serial updates are a
 // large part of it.
-constexpr int kShapes[][2] = {{768, 1}, {512, 2}};
-constexpr int kNumShapes = 2;
+constexpr int kShapes[][2] = {{768, 1}, {512, 2}, {640, 2}, {512, 3}};
+constexpr int kNumShapes = 4;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
 constexpr uint32_t kResSum = 256;                    // residual: threads adding up a large scene's chunks
 constexpr uint32_t kWarpChunks = 1024;               // residual: scenes with at most this many chunks
                                                      // are added by one warp, larger ones by the CTA
 // per contact: ab 8 | (n, la) 16 | (lb, q_n, Sigma_n, f_c) 16 | (mu, rbar mu_r) 8 |
-//              (1/D_n, 1/D_t, 1/D_r, basis reciprocal) 16 |
 //              impulses (n, t1, t2, r.x) 16 | (r.y, r.z) 8
-constexpr size_t kRowBytes = 88;
-constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffRd = 48, kOffLa = 64,
-                 kOffLb = 80;  // x wave size
+constexpr size_t kRowBytes = 72;
+constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffLa = 48, kOffLb = 64;  // x wave size
 __host__ __device__ constexpr size_t stage_bytes(int wave) { return (size_t)wave * kRowBytes; }
-// One contact per thread: the particle records of a colour's second wave are
-// fetched into shared memory (64 B per contact) while its first wave solves.
-constexpr size_t kPrefetchBytes = 64;
-__host__ __device__ constexpr size_t pgs_smem(int wave, int per_thread) {
-  return kStages * stage_bytes(wave) + (per_thread == 1 ? (size_t)wave * kPrefetchBytes : 0);
-}
+__host__ __device__ constexpr size_t pgs_smem(int wave) { return kStages * stage_bytes(wave); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -289,14 +284,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t pari
     }
   }
 }
-
-// 16-byte asynchronous copy global -> shared through L2 (no L1), and its
-// group commit / wait (the issuing thread waits for its own copies).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
                                          unsigned long long *bar) {
@@ -383,13 +370,12 @@ __device__ __forceinline__ void stage_range(const DevPtrs &d, uint32_t p0, uint3
   bulk_g2s(stage + kOffRn * W + 16u * at, d.p_rn + p0, 16u * cnt, bar);
   bulk_g2s(stage + kOffRq * W + 16u * at, d.p_rq + p0, 16u * cnt, bar);
   bulk_g2s(stage + kOffRm * W + 8u * at, d.p_rm + p0, 8u * cnt2, bar);
-  bulk_g2s(stage + kOffRd * W + 16u * at, d.p_rd + p0, 16u * cnt, bar);
   bulk_g2s(stage + kOffLa * W + 16u * at, d.p_la + p0, 16u * cnt, bar);
   bulk_g2s(stage + kOffLb * W + 8u * at, d.p_lb + p0, 8u * cnt2, bar);
 }
 
 __device__ __forceinline__ uint32_t range_bytes(uint32_t cnt) {
-  return cnt ? 4u * 16u * cnt + 3u * 8u * ((cnt + 1u) & ~1u) : 0u;
+  return cnt ? 3u * 16u * cnt + 3u * 8u * ((cnt + 1u) & ~1u) : 0u;
 }
 
 __device__ __forceinline__ void issue_wave(const DevPtrs &d, const WaveSeq &q, const uint32_t *lo,
@@ -455,7 +441,6 @@ template <int kPgsThreads, int kPerThread>
 __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
   constexpr uint32_t kWave = kPgsThreads * kPerThread;  // contacts per wave
   constexpr size_t kStageBytes = stage_bytes(kWave);
-  constexpr bool kPrefetch = kPerThread == 1;
   if (step_failed(d)) return;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ unsigned long long full[kStages];
@@ -558,7 +543,7 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
           Side A, B;
           load_pair(d, r, A, B);
           float3 t1, t2;
-          onb_pre(r.n, r.ob, t1, t2);
+          onb(r.n, t1, t2);
           apply(r, A, B, L0.x, L0.y * t1 + L0.z * t2, make_float3(L0.w, L1.x, L1.y));
           store_side(d, r.ab.x, A);
           if (r.dyn) store_side(d, r.ab.y, B);
@@ -606,7 +591,6 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
         const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);
         const float2 *srm = reinterpret_cast<const float2 *>(stage + kOffRm * kWave);
-        const float4 *srd = reinterpret_cast<const float4 *>(stage + kOffRd * kWave);
         const float4 *sla = reinterpret_cast<const float4 *>(stage + kOffLa * kWave);
         const float2 *slb = reinterpret_cast<const float2 *>(stage + kOffLb * kWave);
         const WaveDesc q = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], w, kWave);
@@ -614,9 +598,6 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
         uint32_t gp[kPerThread];  // colour-order index of each staged contact (or ~0)
         uint32_t qs[kPerThread];  // its scene, once some scene of a batch has stopped
         const bool skip_done = s_ndone != 0u;
-        // the second wave of a colour was fetched during the first
-        const bool from_prefetch = kPrefetch && w == 1;
-        if (from_prefetch) cp_async_wait_all();
         // gathers of every contact of this thread first (disjoint particles)
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
@@ -626,48 +607,11 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
             const uint2 ab = sab[li];
             if (ab.x != 0xFFFFFFFFu) {  // not a padding slot
               if (skip_done) qs[j] = __ldcg(d.sid + ab.x);
-              if (from_prefetch) {
-                const float4 *pb = reinterpret_cast<const float4 *>(smem + kStages * kStageBytes) + 4 * li;
-                A[j] = Side{f3(pb[0]), f3(pb[1]), pb[0].w, pb[1].w};
-                B[j] = Side{f3(pb[2]), f3(pb[3]), pb[2].w, pb[3].w};
-              } else {
-                A[j] = load_side(d, ab.x);
-                if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
-                else B[j] = Side{f3(d.p_sv[gp[j]]), f3(d.p_sw[gp[j]]), 0.f, 0.f};
-              }
+              A[j] = load_side(d, ab.x);
+              if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
+              else B[j] = Side{f3(d.p_sv[gp[j]]), f3(d.p_sw[gp[j]]), 0.f, 0.f};
             }
           }
-        }
-        // first wave of a colour with a second: fetch the second wave's
-        // particle records now (same colour: other particles than this wave's
-        // and than any other CTA's, all final since the neighbour wait); a
-        // static side's record is its point velocity and spin with zero
-        // inverse mass and inertia
-        if (kPrefetch && w == 0 && s_nw[col] > 1) {
-          const uint32_t k1 = consumed + 1u;
-          if (!mbar_wait(&full[k1 % kStages], (k1 / kStages) & 1u, d.err, TDS_BARRIER_NS)) { ok = false; break; }
-          const unsigned char *stage1 = smem + (size_t)(k1 % kStages) * kStageBytes;
-          const uint2 *sab1 = reinterpret_cast<const uint2 *>(stage1 + kOffAb * kWave);
-          const WaveDesc q1 = wave_desc(s_lo[2 * col], s_hi[2 * col], s_lo[2 * col + 1], s_hi[2 * col + 1], 1u, kWave);
-          const uint32_t li = threadIdx.x;
-          const uint32_t g1 =
-              li < q1.n1 ? q1.a1 + li : (li >= q1.n1e && li < q1.n1e + q1.n2 ? q1.a2 + (li - q1.n1e) : ~0u);
-          if (g1 != ~0u) {
-            const uint2 ab = sab1[li];
-            if (ab.x != 0xFFFFFFFFu) {
-              float4 *pb = reinterpret_cast<float4 *>(smem + kStages * kStageBytes) + 4 * li;
-              cp_async16(pb + 0, d.pv + 2 * (size_t)ab.x);
-              cp_async16(pb + 1, d.pv + 2 * (size_t)ab.x + 1);
-              if (is_dyn(ab.y)) {
-                cp_async16(pb + 2, d.pv + 2 * (size_t)ab.y);
-                cp_async16(pb + 3, d.pv + 2 * (size_t)ab.y + 1);
-              } else {
-                cp_async16(pb + 2, d.p_sv + g1);
-                cp_async16(pb + 3, d.p_sw + g1);
-              }
-            }
-          }
-          cp_async_commit();
         }
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
@@ -682,8 +626,6 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
             r.n = f3(rn); r.la = rn.w;
             r.lb = rq.x; r.qn = rq.y; r.Sn = rq.z; r.fc = rq.w;
             r.mu = rm.x; r.rmu = rm.y;
-            const float4 rd = srd[li];
-            r.iDn = rd.x; r.iDt = rd.y; r.iDr = rd.z; r.ob = rd.w;
             r.dyn = is_dyn(r.ab.y);
             float4 L0 = sla[li];
             float2 L1 = slb[li];
@@ -836,9 +778,6 @@ __global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) 
       if (s_flag) break;
     }
   }
-  // a second wave's records still in flight (a solve that stopped on an
-  // error between the two waves of a colour) land before the CTA exits
-  if (kPrefetch) cp_async_wait_all();
   // drain the waves still in flight before the CTA exits (bulk copies of this
   // CTA's own: a fixed, generous limit, whatever the limit on waits for others)
   if (threadIdx.x == 0)
@@ -937,7 +876,6 @@ __global__ void __launch_bounds__(512) k_impact(DevPtrs d, ImpactArgs a) {
           float2 L1 = make_float2(t.x, t.y);
           Side A, B;
           load_pair(d, r, A, B);
-          r.iDn = __frcp_rn(diag_n(r, A, B));  // rigid normal row
           pgs_update(r, A, B, L0, L1, a.sig_t, a.sig_r);
           store_side(d, r.ab.x, A);
           if (r.dyn) store_side(d, r.ab.y, B);
@@ -1097,7 +1035,7 @@ template <int I>
 constexpr PgsKernel pgs_kernel() {
   return k_pgs<kShapes[I][0], kShapes[I][1]>;
 }
-const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>()};
+const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>(), pgs_kernel<2>(), pgs_kernel<3>()};
 
 int tds_pgs_shapes() { return kNumShapes; }
 void tds_pgs_shape(int i, int *threads, int *per_thread) {
@@ -1114,7 +1052,7 @@ cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_i
   void *args[] = {&dd, &a};
   const int T = kShapes[shape][0];
   return cudaLaunchCooperativeKernel((const void *)kPgsKernels[shape], dim3(blocks), dim3(T), args,
-                                     pgs_smem(T * kShapes[shape][1], kShapes[shape][1]), st);
+                                     pgs_smem(T * kShapes[shape][1]), st);
 }
 
 cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
@@ -1133,7 +1071,7 @@ int tds_pgs_setup() {
   int occ_min = 0;
   for (int i = 0; i < kNumShapes; ++i) {
     const int T = kShapes[i][0];
-    const size_t smem = pgs_smem(T * kShapes[i][1], kShapes[i][1]);
+    const size_t smem = pgs_smem(T * kShapes[i][1]);
     if (cudaFuncSetAttribute((const void *)kPgsKernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return 0;

@@ -201,9 +201,9 @@ def test_launch_shapes_give_identical_results(tds, graph, solver):
 
     beds = S.batched(5, scenes=5, n_lo=800, n_hi=4000)
     shapes = [dict(pgs_sync=1), dict(pgs_sync=0), dict(pgs_sync=1, pgs_blocks=7, colour_blocks=13),
-              dict(pgs_sync=0, pgs_blocks=3), dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=2),
+              dict(pgs_sync=0, pgs_blocks=3), dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=3),
               dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=2, pgs_blocks=5),
-              dict(pgs_sync=0, pgs_threads=512, pgs_per_thread=2, pgs_blocks=11)]
+              dict(pgs_sync=0, pgs_threads=640, pgs_per_thread=2)]
     out = []
     for shape in shapes:
         b = tds.Batch(beds, stream=torch.cuda.Stream())
@@ -288,7 +288,7 @@ def test_every_bed_stops_at_its_own_residual(tds, graph):
     and the same state, bit for bit, over several steps with moving tools."""
     import torch
 
-    tol, every, steps = 1e-4, 5, 3
+    tol, every, steps = 1e-3, 5, 3
     scenes = [packed_scene(900, 41, mu_t=0.5, mu_r=0.1, iters=3000, tol=tol),
               packed_scene(1900, 42, mu_t=0.7, mu_r=0.2, iters=3000, tol=tol),
               packed_scene(400, 43, mu_t=0.9, mu_r=0.0, iters=3000, tol=tol),
