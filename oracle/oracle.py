@@ -48,6 +48,7 @@ class OrcParams(ctypes.Structure):
         ("tool_vel", ctypes.c_float * 3), ("tool_angvel", ctypes.c_float * 3),
         ("restitution", ctypes.c_double), ("impact_speed", ctypes.c_double),
         ("impact_iters", ctypes.c_int32), ("threads", ctypes.c_int32),
+        ("recolour_every", ctypes.c_int32),
     ]
 
 
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.orc_step.argtypes = [P(OrcParams), ctypes.c_int32, P(ctypes.c_double),
                                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                                ctypes.c_int32, P(ctypes.c_uint64), P(ctypes.c_double),
+                               P(ctypes.c_int32), ctypes.c_int32,
                                ctypes.c_int32, P(ctypes.c_uint64), P(ctypes.c_double),
                                P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_double),
                                P(ctypes.c_double), P(OrcStats)]
@@ -128,6 +130,7 @@ class Params:
         p.impact_speed = float(s.get("impact_speed", 0.0))
         p.impact_iters = int(s.get("impact_iters", 0))
         p.threads = int(s.get("threads", 1))
+        p.recolour_every = int(s.get("recolour_every", 1))
         hf = s.get("hf")
         if hf is not None:
             h = _f32(hf["h"]).reshape(-1)
@@ -182,6 +185,8 @@ class State:
         self.r = _f64(scene["r"]).copy()
         self.prev_keys = np.zeros(0, dtype=np.uint64)
         self.prev_lam = np.zeros((0, 7), dtype=np.float64)
+        self.prev_colour = np.zeros(0, dtype=np.int32)
+        self.steps = 0  # steps taken
 
 
 def step(scene: dict, state: State, tool=None, **override) -> dict:
@@ -191,6 +196,10 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
     n = state.x.shape[0]
     cap = max(64, 16 * n)
     st = OrcStats()
+    prev_colour = state.prev_colour
+    if len(prev_colour) != len(state.prev_keys):  # colours unknown: every contact is coloured anew
+        prev_colour = np.full(len(state.prev_keys), -1, np.int32)
+    prev_colour = np.ascontiguousarray(prev_colour, np.int32)
     while True:
         keys = np.zeros(cap, dtype=np.uint64)
         lam = np.zeros((cap, 7), dtype=np.float64)
@@ -203,7 +212,8 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
                             _ptr(v0, ctypes.c_double), _ptr(w0, ctypes.c_double),
                             _ptr(state.r, ctypes.c_double), len(state.prev_keys),
                             _ptr(state.prev_keys, ctypes.c_uint64),
-                            _ptr(state.prev_lam, ctypes.c_double), cap,
+                            _ptr(state.prev_lam, ctypes.c_double),
+                            _ptr(prev_colour, ctypes.c_int32), int(state.steps), cap,
                             _ptr(keys, ctypes.c_uint64), _ptr(lam, ctypes.c_double),
                             _ptr(col, ctypes.c_int32), _ptr(dl, ctypes.c_double),
                             _ptr(ft, ctypes.c_double), _ptr(tg, ctypes.c_double),
@@ -218,6 +228,8 @@ def step(scene: dict, state: State, tool=None, **override) -> dict:
     state.x, state.v, state.w = x0, v0, w0
     state.prev_keys = keys[:nc].copy()
     state.prev_lam = lam[:nc].copy()
+    state.prev_colour = col[:nc].copy()
+    state.steps += 1
     return {
         "keys": keys[:nc].copy(), "lam": lam[:nc].copy(), "colour": col[:nc].copy(),
         "delta": dl[:nc].copy(), "features": ft[:nc].copy(), "targets": tg[:nc].copy(),

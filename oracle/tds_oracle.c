@@ -357,6 +357,7 @@ typedef struct {
   double ln, lt[2], lr[3];        /* impulses */
   double Gvn;                     /* G_n v_n at the start of the step */
   int colour;
+  int kept_colour;                /* incremental colouring: the previous step's colour, or -1 */
   int persisted;                  /* the key existed in the previous step */
   double W;                       /* impulse scale m_eff |g| h of the learned warm start */
   double sdir[3];                 /* slip direction s of the learned warm start */
@@ -661,6 +662,12 @@ static double residual(const contact *C, int nc, const double *v, const double *
 /* Colouring: colour(c) = smallest colour not used by a neighbour of    */
 /* higher priority (neighbours share a dynamic particle). Computed by   */
 /* plain sequential greedy colouring in decreasing priority order.      */
+/* Incremental steps keep the colour of every contact whose key existed */
+/* in the previous step (two such contacts share a particle now iff     */
+/* they did then, so the kept colours stay a proper colouring) and      */
+/* colour only the new contacts, greedily in decreasing priority: the   */
+/* smallest colour used by no neighbour that is kept or new and of      */
+/* higher priority.                                                     */
 /* ------------------------------------------------------------------ */
 static contact *g_sort_base;
 static int cmp_prio_desc(const void *pa, const void *pb) {
@@ -686,7 +693,7 @@ static int colour_contacts(contact *C, int nc, int n) {
     inc[start[C[k].a] + fill[C[k].a]++] = k;
     if (C[k].b >= 0) inc[start[C[k].b] + fill[C[k].b]++] = k;
   }
-  for (int k = 0; k < nc; ++k) { ord[k] = k; C[k].colour = -1; }
+  for (int k = 0; k < nc; ++k) { ord[k] = k; C[k].colour = C[k].kept_colour; }
   g_sort_base = C;
   qsort(ord, nc, sizeof(int), cmp_prio_desc);
   {
@@ -695,12 +702,16 @@ static int colour_contacts(contact *C, int nc, int n) {
     if (!used) { ncol = -1; goto out; }
     for (int o = 0; o < nc; ++o) {
       contact *c = &C[ord[o]];
+      if (c->colour >= 0) {  /* kept from the previous step */
+        if (c->colour + 1 > ncol) ncol = c->colour + 1;
+        continue;
+      }
       int ends[2] = {c->a, c->b};
       for (int e = 0; e < 2; ++e) {
         if (ends[e] < 0) continue;
         for (int m = start[ends[e]]; m < start[ends[e] + 1]; ++m) {
           int col = C[inc[m]].colour;
-          if (col < 0) continue; /* not yet coloured: lower priority */
+          if (col < 0) continue; /* not yet coloured: a new contact of lower priority */
           if (col >= cap) {
             int ncap = 2 * col + 2;
             unsigned char *nu = (unsigned char *)realloc(used, ncap);
@@ -895,11 +906,16 @@ static int impact_stage(const orc_params *P, contact *C, int nc, const int *orde
 
 int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w,
                  const double *r, int32_t n_prev, const uint64_t *prev_keys,
-                 const double *prev_lam, int32_t cap, uint64_t *out_keys,
+                 const double *prev_lam, const int32_t *prev_colour, int32_t step_index,
+                 int32_t cap, uint64_t *out_keys,
                  double *out_lam, int32_t *out_colour, double *out_delta,
                  double *out_feat, double *out_targ, orc_stats *st) {
   if (!P || n < 0 || cap < 0 || !st || (n > 0 && (!x || !v || !w || !r))) return -2;
   if (n_prev > 0 && (!prev_keys || !prev_lam)) return -2;
+  /* incremental colouring: every step but each recolour_every-th (counting
+   * from the first, step_index 0) keeps the previous step's colours */
+  const int incremental = P->recolour_every > 1 && step_index > 0 && step_index % P->recolour_every != 0;
+  if (incremental && n_prev > 0 && !prev_colour) return -2;
   memset(st, 0, sizeof(*st));
   int rc = 0, nb = 0;
   double h = P->dt;
@@ -950,6 +966,11 @@ int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w
     }
     contact_geometry(P, B, x, r, c);
     contact_rows(P, r, &M, v0, c);
+    c->kept_colour = -1;
+    if (incremental && n_prev > 0) {
+      int j = find_key(n_prev, prev_keys, c->key);
+      if (j >= 0) c->kept_colour = prev_colour[j];
+    }
   }
   free(v0);
   /* 2. p = M v_n + h f: v^* = v_n + h g (gravity is the only external force) */

@@ -67,6 +67,11 @@ typedef struct {
   /* threads updating the contacts of one colour at a time (<= 1: one; a
    * timing option, the results are the same bit for bit; colour order only) */
   int32_t threads;
+  /* colouring: every recolour_every-th step (and the first) colours every
+   * contact; the steps between keep the previous step's colour of each
+   * contact whose key existed then and colour only the new ones (<= 1: every
+   * step colours every contact) */
+  int32_t recolour_every;
 } orc_params;
 
 typedef struct {
@@ -91,13 +96,16 @@ int32_t orc_find_contacts(const orc_params *P, int32_t n, const double *x,
 
 /* One time step, in place on x, v, w (n*3 each, FP64); r: radii.
  * prev_keys (ascending) / prev_lam (7 per key: Lambda_n, Lambda_t world xyz,
- * Lambda_r xyz) give the previous step's impulses for the warm start.
+ * Lambda_r xyz) / prev_colour give the previous step's impulses for the warm
+ * start and its colours for incremental colouring; step_index counts the
+ * steps taken before this one.
  * Outputs, in ascending key order, up to cap contacts: keys, lam (7 each),
  * colour, delta (overlap). Returns 0, -1 if cap is too small, -2 on bad
  * arguments or allocation failure. */
 int32_t orc_step(const orc_params *P, int32_t n, double *x, double *v, double *w,
                  const double *r, int32_t n_prev, const uint64_t *prev_keys,
-                 const double *prev_lam, int32_t cap, uint64_t *out_keys,
+                 const double *prev_lam, const int32_t *prev_colour, int32_t step_index,
+                 int32_t cap, uint64_t *out_keys,
                  double *out_lam, int32_t *out_colour, double *out_delta,
                  double *out_feat, double *out_targ, orc_stats *st);
 

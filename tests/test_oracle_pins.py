@@ -542,3 +542,60 @@ def test_threaded_colour_sweep_is_bitwise_the_serial_one(orc):
     assert ra["iterations"] == rb["iterations"] and ra["residual"] == rb["residual"]
     assert np.array_equal(ra["lam"], rb["lam"])
     assert np.array_equal(sa.x, sb.x) and np.array_equal(sa.v, sb.v) and np.array_equal(sa.w, sb.w)
+
+
+def _greedy_violations(keys, col, prio, kept):
+    """Checks of a colouring against its definition: proper, and every
+    contact not kept has the smallest colour unused by its neighbours that
+    are kept or of higher priority. Returns the number of violations."""
+    a = (keys >> np.uint64(32)).astype(np.int64)
+    lo = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    b = np.where(lo & S_BIT, -1, lo)
+    inc = {}
+    for c in range(len(keys)):
+        for p in (a[c], b[c]):
+            if p >= 0:
+                inc.setdefault(int(p), []).append(c)
+    bad = 0
+    for c in range(len(keys)):
+        nb = set()
+        for p in (a[c], b[c]):
+            if p >= 0:
+                nb.update(inc[int(p)])
+        nb.discard(c)
+        bad += any(col[d] == col[c] for d in nb)
+        if not kept[c]:
+            used = {int(col[d]) for d in nb if kept[d] or prio[d] > prio[c]}
+            smallest = next(k for k in range(len(nb) + 2) if k not in used)
+            bad += int(col[c]) != smallest
+    return bad
+
+
+def test_incremental_colouring_keeps_colours_and_colours_new_contacts_greedily(orc):
+    """With recolour_every = 4: steps 0 and 4 colour every contact greedily in
+    priority order; steps 1-3 keep the previous colour of every persisting
+    key and give each new contact the smallest colour that no kept neighbour
+    and no new neighbour of higher priority uses."""
+    x, r, v, w = S.packed_block(500, 0.02, 0.03, 14, vel_scale=0.3)
+    s = S.with_particles(S.base_params(iters=10, cohesion=1000.0, recolour_every=4,
+                                       hf=S.flat_heightfield(10, 10, 0, 0, 0.05, 0.05)), x, r, v, w)
+    st = orc.State(s)
+    prev = None
+    new_total = 0
+    for step in range(6):
+        res = orc.step(s, st)
+        keys, col = res["keys"], res["colour"]
+        prio = np.array([orc.priority(int(k)) for k in keys], dtype=np.uint64)
+        incremental = step % 4 != 0
+        if incremental:
+            pk, pc = prev
+            pos = np.searchsorted(pk, keys)
+            kept = (pos < len(pk)) & (pk[np.minimum(pos, len(pk) - 1)] == keys)
+            assert np.array_equal(col[kept], pc[pos[kept]])  # persisting contacts keep their colour
+            new_total += int((~kept).sum())
+        else:
+            kept = np.zeros(len(keys), bool)
+        assert _greedy_violations(keys, col, prio, kept) == 0, step
+        assert res["n_colours"] == col.max() + 1
+        prev = (keys, col)
+    assert new_total > 20  # the case does create new contacts in the incremental steps
