@@ -103,6 +103,8 @@ def parse():
                          "(-1: the workload's fixed sweep count, 0: no second region)")
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cold", action="store_true", help="cold start instead of previous-step impulses")
+    ap.add_argument("--recolour-period", type=int, default=1,
+                    help="colour every contact every k-th step, only the new contacts in between (1: every step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -219,6 +221,7 @@ def _apply_args(scene: dict, args) -> dict:
         scene["residual_every"] = 0  # adaptive check schedule (same stopping criterion)
     if args.cold:
         scene["warm_start"] = 0
+    scene["recolour_every"] = args.recolour_period
     return scene
 
 

@@ -183,6 +183,19 @@ tds_status tds_set_solver(tds_scene *s, uint32_t max_iters, float tol, uint32_t 
  * tds_scene_desc) for the following steps. */
 tds_status tds_set_impact(tds_scene *s, float restitution, float impact_speed, uint32_t impact_iters);
 
+/* Colouring of the contact graph (the order of the projected Gauss-Seidel
+ * sweep): every period-th step (counting from the scene's first, step 0)
+ * colours every contact greedily in hashed-priority order; the steps between
+ * keep, for each contact whose key existed in the previous step, that step's
+ * colour (two such contacts share a particle now iff they did then, so the
+ * kept colours stay proper) and colour only the new contacts, each with the
+ * smallest colour that no kept neighbour and no new neighbour of higher
+ * priority uses. 1 (the default) colours every contact every step. The step
+ * counter is that of tds_get_stats (restored with a checkpoint or a
+ * rollback), so a scene's colourings do not depend on how its steps were
+ * issued. */
+tds_status tds_set_recolour_period(tds_scene *s, uint32_t period);
+
 /* Change the warm start (tds_warm_start) for the following steps;
  * TDS_WARM_LEARNED needs tds_set_mlp_weights before the next step. */
 tds_status tds_set_warm_start(tds_scene *s, int32_t mode);

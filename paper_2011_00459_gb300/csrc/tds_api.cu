@@ -133,9 +133,10 @@ struct GraphKey {
   uint32_t max_iters = 0, every = 0, impact_iters = 0;
   float tol = -1.f, restitution = -1.f, impact_speed = -1.f;
   unsigned long long wait_ns = 0;
+  uint32_t recolour = 0;
   bool operator==(const GraphKey &o) const {
     return use_prev == o.use_prev && warm == o.warm && recording == o.recording && timing == o.timing &&
-           wait_ns == o.wait_ns &&
+           wait_ns == o.wait_ns && recolour == o.recolour &&
            pgs_blocks == o.pgs_blocks && pgs_sync == o.pgs_sync && pgs_shape == o.pgs_shape &&
            colour_blocks == o.colour_blocks &&
            max_iters == o.max_iters && every == o.every && tol == o.tol && impact_iters == o.impact_iters &&
@@ -710,6 +711,7 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
   carve(c, s->L, s->d, s->x, 64 * sms);
   s->d.targ = nullptr;
   s->d.wait_ns = TDS_BARRIER_NS;
+  s->d.recolour = 1u;
   // common constants
   const tds_scene_desc &D = descs[0];
   StepConsts &k = s->k;
@@ -885,6 +887,7 @@ GraphKey graph_key(const tds_scene *s) {
   g.impact_speed = s->desc.impact_speed;
   g.cutter = s->any_cutter;
   g.wait_ns = s->d.wait_ns;
+  g.recolour = s->d.recolour;
   return g;
 }
 
@@ -1130,6 +1133,13 @@ tds_status tds_set_impact(tds_scene *s, float restitution, float impact_speed, u
   s->desc.restitution = restitution;
   s->desc.impact_speed = impact_speed;
   s->desc.impact_iters = impact_iters;
+  return TDS_OK;
+}
+
+tds_status tds_set_recolour_period(tds_scene *s, uint32_t period) {
+  if (!s) return fail(TDS_ERR_INVALID_ARG, "scene is NULL");
+  if (period == 0) return fail(TDS_ERR_INVALID_ARG, "period must be >= 1");
+  s->d.recolour = period;
   return TDS_OK;
 }
 

@@ -62,10 +62,24 @@ __device__ __forceinline__ uint32_t frontier_slot(uint32_t *counter) {
   return base + (uint32_t)__popc(mask & ((1u << lane) - 1u));
 }
 
-// wait[c] = number of neighbours of higher priority; sources start round 0.
+// wait[c] = number of uncoloured neighbours of higher priority; sources
+// start round 0. A full colouring starts with every contact uncoloured; an
+// incremental one (see incremental_colouring) with the colours the
+// narrowphase kept, which also enter the colour count.
 __global__ void k_colour_init(DevPtrs d) {
   const uint32_t nc = d.ctr[CTR_NC];
+  const bool inc = incremental_colouring(d);
+  __shared__ uint32_t s_maxcol;
+  if (threadIdx.x == 0) s_maxcol = 0;
+  __syncthreads();
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x) {
+    if (inc) {
+      const uint32_t kept = d.colour[c];
+      if (kept != TDS_NO_COLOUR) {
+        atomicMax(&s_maxcol, kept + 1u);
+        continue;
+      }
+    }
     uint2 ab = d.c_ab[c];
     unsigned long long pc = d.prio[c];
     int32_t w = 0;
@@ -78,16 +92,19 @@ __global__ void k_colour_init(DevPtrs d) {
 #pragma unroll
         for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
 #pragma unroll
-        for (int q = 0; q < kBatch; ++q) w += (ent[q].x != c && higher(d, ent[q], pc)) ? 1 : 0;
+        for (int q = 0; q < kBatch; ++q)
+          w += (ent[q].x != c && higher(d, ent[q], pc) && (!inc || d.colour[ent[q].x] == TDS_NO_COLOUR)) ? 1 : 0;
       }
     }
     d.wait[c] = w;
-    d.colour[c] = TDS_NO_COLOUR;
+    if (!inc) d.colour[c] = TDS_NO_COLOUR;
     if (w == 0) {
       const uint32_t q = frontier_slot(d.ctr + CTR_FCOUNT);
       if (q < nc) d.frontier0[q] = c;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_maxcol) atomicMax(d.ctr + CTR_NCOL, s_maxcol);
 }
 
 // Persistent, co-resident launch: one round per grid barrier. A round colours
@@ -96,6 +113,7 @@ __global__ void k_colour_init(DevPtrs d) {
 __global__ void k_colour_rounds(DevPtrs d) {
   const uint32_t stride = gridDim.x * blockDim.x;
   const uint32_t nc = d.ctr[CTR_NC];
+  const bool inc = incremental_colouring(d);
   __shared__ uint32_t s_maxcol;
   if (threadIdx.x == 0) s_maxcol = 0;
   __syncthreads();
@@ -123,8 +141,11 @@ __global__ void k_colour_rounds(DevPtrs d) {
 #pragma unroll
           for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
 #pragma unroll
+          // a full colouring reads its higher-priority neighbours (all
+          // coloured by now); an incremental one also the kept colours of
+          // lower priority (its uncoloured neighbours read as no colour)
           for (int q = 0; q < kBatch; ++q)
-            col[q] = (ent[q].x != c && higher(d, ent[q], pc)) ? (uint32_t)__ldcg(d.colour + ent[q].x) : 0xFFu;
+            col[q] = (ent[q].x != c && (inc || higher(d, ent[q], pc))) ? (uint32_t)__ldcg(d.colour + ent[q].x) : 0xFFu;
 #pragma unroll
           for (int q = 0; q < kBatch; ++q) {
             if (col[q] < 64) used0 |= 1ull << col[q];
@@ -149,8 +170,13 @@ __global__ void k_colour_rounds(DevPtrs d) {
 #pragma unroll
           for (int q = 0; q < kBatch; ++q) ent[q] = m0 + q < e ? d.inc_ent[m0 + q] : make_uint2(c, 0u);
 #pragma unroll
+          // (an incremental colouring releases only uncoloured neighbours:
+          // a kept contact waits for nothing)
           for (int q = 0; q < kBatch; ++q)
-            old[q] = (ent[q].x != c && !higher(d, ent[q], pc)) ? atomicSub(d.wait + ent[q].x, 1) : 0;
+            old[q] = (ent[q].x != c && !higher(d, ent[q], pc) &&
+                      (!inc || __ldcg(d.colour + ent[q].x) == TDS_NO_COLOUR))
+                         ? atomicSub(d.wait + ent[q].x, 1)
+                         : 0;
 #pragma unroll
           for (int q = 0; q < kBatch; ++q)
             if (old[q] == 1) {

@@ -218,6 +218,7 @@ struct Writer {
   float4 P, Va;
   int use_prev;
   uint32_t pf, pc;
+  bool inc;  // incremental colouring: contacts of a previous key keep its colour
 
   // Common part of every contact: rows and warm start. n points from a
   // towards b (into a static surface), delta is the overlap, vb/wb the other
@@ -259,10 +260,13 @@ struct Writer {
     float4 la0 = make_float4(0.f, 0.f, 0.f, 0.f);
     float2 lb0 = make_float2(0.f, 0.f);
     uint8_t persisted = 0;
-    if (use_prev) {
+    uint32_t kept = TDS_NO_COLOUR;
+    if (use_prev || inc) {
       for (uint32_t q = pf; q < pf + pc; ++q) {
         if (__ldg(d.prev_other[0] + q) != other) continue;
         float4 l0 = d.prev_l0[0][q], l1 = d.prev_l1[0][q];
+        kept = __float_as_uint(l1.w);  // the key's colour in the previous step
+        if (!use_prev) break;
         float ln = fmaxf(l0.x, -fc);
         float3 t1, t2;
         onb(n, t1, t2);
@@ -282,6 +286,7 @@ struct Writer {
     d.c_la[c] = la0;
     d.c_lb[c] = lb0;
     d.c_flag[c] = persisted;
+    if (inc) d.colour[c] = (uint8_t)(kept < TDS_MAX_COLOURS ? kept : TDS_NO_COLOUR);
   }
 
   __device__ void pair(uint32_t j, uint32_t pj, float4 Q) {
@@ -344,9 +349,10 @@ struct Writer {
 };
 
 __global__ void k_write(DevPtrs d, StepConsts k, int use_prev) {
+  const bool inc = incremental_colouring(d);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k.n; i += gridDim.x * blockDim.x) {
-    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.pv[2 * i], use_prev, 0u, 0u};
-    if (use_prev) {
+    Writer w{d, k, i, d.pid[i], d.cstart[i], d.pos[i], d.pv[2 * i], use_prev, 0u, 0u, inc};
+    if (use_prev || inc) {
       w.pf = d.prev_first[0][w.me];
       w.pc = d.prev_cnt[0][w.me];
     }

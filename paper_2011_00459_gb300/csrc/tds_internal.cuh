@@ -137,6 +137,7 @@ struct DevPtrs {
   uint32_t *prev_first[2], *prev_cnt[2], *prev_other[2];
   float4 *prev_l0[2], *prev_l1[2];
   // scalars and scratch
+  uint32_t recolour;          // colour every contact every recolour-th step (1: every step)
   unsigned long long wait_ns; // limit of every wait on other CTAs (grid barriers, neighbour flags)
                               // before the wait gives up and latches DEV_ERR_BARRIER
   int32_t *err;
@@ -258,6 +259,16 @@ __device__ __forceinline__ unsigned long long priority(unsigned long long key) {
 // an error is latched. The state buffers of the failing step's start then
 // stay intact for the host to restore.
 __device__ __forceinline__ bool step_failed(const DevPtrs &d) { return *(volatile const int32_t *)d.err != 0; }
+
+// Incremental colouring this step: the contacts whose key existed in the
+// previous step keep its colour, only the new ones are coloured (every step
+// but each recolour-th, counting from the first). The step's index is the
+// count of steps that started clean (the broadphase's first kernel counts
+// this one), so graph replays take the same decision as launches.
+__device__ __forceinline__ bool incremental_colouring(const DevPtrs &d) {
+  const uint32_t idx = *(volatile const uint32_t *)(d.ctr + CTR_CLEAN) - 1u;
+  return d.recolour > 1u && idx > 0u && idx % d.recolour != 0u;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;

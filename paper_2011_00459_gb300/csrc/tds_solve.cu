@@ -910,7 +910,7 @@ __global__ void k_writeback(DevPtrs d) {
     float3 tw = L0.y * t1 + L0.z * t2;
     d.prev_other[1][c] = (uint32_t)(d.c_key[c] & 0xFFFFFFFFull);
     d.prev_l0[1][c] = make_float4(L0.x, tw.x, tw.y, tw.z);
-    d.prev_l1[1][c] = make_float4(L0.w, L1.x, L1.y, 0.f);
+    d.prev_l1[1][c] = make_float4(L0.w, L1.x, L1.y, __uint_as_float((uint32_t)d.colour[c]));  // + its colour
     if (d.targ) {  // training targets of the learned warm start (final impulses in the slip frame)
       const float4 sw = d.sdirw[c];
       const float3 s = f3(sw);

@@ -34,7 +34,8 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_graph", "tds_batch_set_tool_poses", "tds_get_launch_config",
             "tds_set_launch_config", "tds_aggregate_bodies", "tds_coarse_grain", "tds_advect_fluid",
             "tds_set_impact", "tds_set_cutter", "tds_read_heightfield", "tds_read_radii",
-            "tds_state_bytes", "tds_save_state", "tds_load_state", "tds_batch_read_solve"]
+            "tds_state_bytes", "tds_save_state", "tds_load_state", "tds_batch_read_solve",
+            "tds_set_recolour_period"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
 SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes compiled (threads, contacts per thread)
@@ -173,6 +174,7 @@ def lib() -> ctypes.CDLL:
         L.tds_set_mlp_weights.argtypes = [vp, vp, ctypes.c_uint32]
         L.tds_set_recording.argtypes = [vp, ctypes.c_int32]
         L.tds_set_warm_start.argtypes = [vp, ctypes.c_int32]
+        L.tds_set_recolour_period.argtypes = [vp, ctypes.c_uint32]
         L.tds_set_impact.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_uint32]
         L.tds_set_cutter.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(Cutter)]
         L.tds_read_heightfield.argtypes = [vp, ctypes.c_uint32, vp, vp, ctypes.c_uint32]
@@ -335,6 +337,9 @@ class Scene:
             _check(L.tds_create_batch(descs, count, ws_ptr, ws_bytes,
                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
+        period = int(scenes[0].get("recolour_every", 1))
+        if period != 1:
+            self.set_recolour_period(period)
 
     # -- calls ---------------------------------------------------------------
     def set_tool_pose(self, tool: dict):
@@ -451,6 +456,11 @@ class Scene:
 
     def set_warm_start(self, mode: int):
         _check(lib().tds_set_warm_start(self.h, int(mode)))
+
+    def set_recolour_period(self, period: int):
+        """Colour every contact every ``period``-th step; in the steps between
+        persisting contacts keep their colour and only new ones are coloured."""
+        _check(lib().tds_set_recolour_period(self.h, int(period)))
 
     def set_recording(self, enable: bool = True):
         _check(lib().tds_set_recording(self.h, int(enable)))

@@ -10,7 +10,7 @@ from paper_2011_00459_gb300 import scenes as S
 
 def packed_scene(n: int, seed: int, cohesion: float = 1000.0, mu_t: float = 0.6,
                  mu_r: float = 0.1, iters: int = 50, tool: bool = True, r_lo: float = 0.02,
-                 r_hi: float = 0.03, tol: float = 0.0) -> dict:
+                 r_hi: float = 0.03, tol: float = 0.0, **extra) -> dict:
     x, r, v, w = S.packed_block(n, r_lo, r_hi, seed, vel_scale=0.1)
     lo = x.min(0) - r_hi
     hi = x.max(0) + r_hi
@@ -23,7 +23,7 @@ def packed_scene(n: int, seed: int, cohesion: float = 1000.0, mu_t: float = 0.6,
     hf["h"] = hf["h"] + np.float32(lo[2] + 0.5 * r_hi)
     p = S.base_params(cohesion=cohesion, mu_t=mu_t, mu_r=mu_r, iters=iters, tol=tol,
                       residual_every=5, hf=hf,
-                      walls=S.bed_walls(lx, ly, 2.0, float(lo[0]), float(lo[1])))
+                      walls=S.bed_walls(lx, ly, 2.0, float(lo[0]), float(lo[1])), **extra)
     if tool:
         p["tool_boxes"] = np.concatenate([S.blade(0.6 * ly, 0.2, 0.02),
                                           S.box((0.05, 0.0, 0.12), (0.04, 0.1, 0.02))[None]])
