@@ -103,7 +103,7 @@ def parse():
                          "(-1: the workload's fixed sweep count, 0: no second region)")
     ap.add_argument("--max-iters", type=int, default=2000)
     ap.add_argument("--cold", action="store_true", help="cold start instead of previous-step impulses")
-    ap.add_argument("--recolour-period", type=int, default=1,
+    ap.add_argument("--recolour-period", type=int, default=16,
                     help="colour every contact every k-th step, only the new contacts in between (1: every step)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -238,8 +238,11 @@ def make_workload(args, rank: int):
 
 
 def _solve_desc(scene: dict) -> str:
+    k = int(scene.get("recolour_every", 1))
+    colouring = (", every contact coloured every step" if k <= 1 else
+                 f", every contact coloured every {k}th step and only the new contacts in between")
     return (f"residual <= {scene['tol']:g} (cap {scene['iters']} sweeps)" if scene.get("tol", 0) > 0
-            else f"{scene['iters']} sweeps")
+            else f"{scene['iters']} sweeps") + colouring
 
 
 def describe(work, args) -> dict:
