@@ -85,6 +85,7 @@ def parse():
     ap.add_argument("--pgs-sync", type=int, default=-1, choices=[-1, 0, 1],
                     help="solver sync between colours: 1 neighbour, 0 grid barrier (-1: library default)")
     ap.add_argument("--pgs-blocks", type=int, default=0, help="solver CTAs (0: library default)")
+    ap.add_argument("--pgs-shape", default="", help="solver CTA shape THREADSxPER_THREAD (e.g. 384x1)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes (no untimed tuning before warm-up)")
     ap.add_argument("--no-forms", action="store_true",
@@ -546,8 +547,10 @@ def prepare(args, work, tds, S, stream, replay=None):
     def between() -> int:
         """Sets the launch shapes during the settle; returns the settle steps taken."""
         g = sim.g
-        if args.pgs_sync >= 0 or args.pgs_blocks:
-            g.set_launch_config(pgs_blocks=args.pgs_blocks, pgs_sync=None if args.pgs_sync < 0 else args.pgs_sync)
+        if args.pgs_sync >= 0 or args.pgs_blocks or args.pgs_shape:
+            t, per = (int(v) for v in args.pgs_shape.split("x")) if args.pgs_shape else (0, 0)
+            g.set_launch_config(pgs_blocks=args.pgs_blocks, pgs_sync=None if args.pgs_sync < 0 else args.pgs_sync,
+                                pgs_threads=t, pgs_per_thread=per)
         elif replay is not None:
             g.set_launch_config(**replay["shape"])
             tuned.update(replay)

@@ -441,8 +441,11 @@ tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
  * with a grid barrier (0); colour_blocks: persistent colouring CTAs;
  * pgs_threads x pgs_per_thread: the solver CTA's threads and contacts per
  * thread, one of the compiled shapes 768x1 (the default), 512x2, 640x2,
- * 512x3 (both 0 keep the current shape).
- * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits.
+ * 512x3 (one CTA per SM) and 384x1 (two CTAs per SM) (both 0 keep the current
+ * shape).
+ * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits
+ * (max_pgs_blocks for the current solver shape; a shape change with
+ * pgs_blocks 0 lowers the solver CTAs to the new shape's limit if needed).
  * wait_limit_us: how long [microseconds] any CTA of the step's persistent
  * kernels waits for other CTAs (a grid barrier, a neighbour's progress flag)
  * before it gives up: it latches TDS_ERR_BARRIER_TIMEOUT, every

@@ -39,6 +39,7 @@ int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaS
 int tds_launch_cut(const DevPtrs &d, const StepConsts &k, float *heights, uint32_t nh, cudaStream_t st);
 void tds_launch_stage(const DevPtrs &d, uint32_t n, cudaStream_t st);
 int tds_pgs_setup();
+int tds_pgs_occupancy(int i);
 int tds_launch_aggregate(const DevPtrs &d, uint32_t n, const tds_zone *zones, uint32_t nz, uint8_t *zone_id,
                          double *sums, tds_aggregate *out, cudaStream_t st);
 size_t tds_aggregate_sums_words();
@@ -177,6 +178,7 @@ struct tds_scene {
   int pgs_shape = 0;      // solver CTA shape (index of the compiled shapes)
   bool any_cutter = false;
   int max_pgs_blocks = 1, max_colour_blocks = 1;
+  int sms = 1;
   uint64_t steps = 0;
   tds_status latched = TDS_OK;
   uint64_t launches = 0;
@@ -684,10 +686,10 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
                                 "registers)");
     return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
   }
+  s->sms = sms;
   s->pgs_blocks = pgs_blocks_for(s->L.n, sms);  // one co-resident CTA per SM at most
   s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
-  s->max_pgs_blocks = sms * occ_pgs;
-  if (s->max_pgs_blocks > 64 * sms) s->max_pgs_blocks = 64 * sms;
+  s->max_pgs_blocks = 64 * sms;  // the workspace's limit; each shape's co-residency limits it further
   s->max_colour_blocks = sms * occ_col;
   Carver probe{nullptr};
   DevPtrs tmp{};
@@ -1156,7 +1158,7 @@ tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out) {
   out->pgs_blocks = s->pgs_blocks;
   out->pgs_sync = s->pgs_sync;
   out->colour_blocks = s->colour_blocks;
-  out->max_pgs_blocks = s->max_pgs_blocks;
+  out->max_pgs_blocks = std::min(s->max_pgs_blocks, s->sms * tds_pgs_occupancy(s->pgs_shape));
   out->max_colour_blocks = s->max_colour_blocks;
   tds_pgs_shape(s->pgs_shape, &out->pgs_threads, &out->pgs_per_thread);
   out->wait_limit_us = (int32_t)(s->d.wait_ns / 1000ull);
@@ -1165,7 +1167,7 @@ tds_status tds_get_launch_config(tds_scene *s, tds_launch_config *out) {
 
 tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
   if (!s || !cfg) return fail(TDS_ERR_INVALID_ARG, "NULL argument");
-  if (cfg->pgs_blocks < 0 || cfg->pgs_blocks > s->max_pgs_blocks || cfg->colour_blocks < 0 ||
+  if (cfg->pgs_blocks < 0 || cfg->colour_blocks < 0 ||
       cfg->colour_blocks > s->max_colour_blocks || (cfg->pgs_sync != 0 && cfg->pgs_sync != 1) ||
       cfg->wait_limit_us < 0)
     return fail(TDS_ERR_INVALID_ARG,
@@ -1190,7 +1192,14 @@ tds_status tds_set_launch_config(tds_scene *s, const tds_launch_config *cfg) {
                                            ") or both 0");
     }
   }
+  // the solver CTAs must all be co-resident: at most the SMs times the
+  // chosen shape's CTAs per SM
+  const int max_blocks = std::min(64 * s->sms, s->sms * tds_pgs_occupancy(shape));
+  if (cfg->pgs_blocks > max_blocks)
+    return fail(TDS_ERR_INVALID_ARG, "pgs_blocks exceeds the co-resident CTAs of that solver shape (" +
+                                         std::to_string(max_blocks) + ")");
   if (cfg->pgs_blocks) s->pgs_blocks = cfg->pgs_blocks;
+  else if (s->pgs_blocks > max_blocks) s->pgs_blocks = max_blocks;
   if (cfg->colour_blocks) s->colour_blocks = cfg->colour_blocks;
   if (cfg->wait_limit_us) s->d.wait_ns = 1000ull * (unsigned long long)cfg->wait_limit_us;
   s->pgs_sync = cfg->pgs_sync;

@@ -237,8 +237,10 @@ struct SolveArgs {
 // 1M bed and the batch, one contact per thread over 768 threads is fastest:
 // each colour phase is a latency chain, and a thread's serial updates are a
 // large part of it.
-constexpr int kShapes[][2] = {{768, 1}, {512, 2}, {640, 2}, {512, 3}};
-constexpr int kNumShapes = 4;
+// (threads, contacts per thread, co-resident CTAs per SM the register budget
+// is sized for)
+constexpr int kShapes[][3] = {{768, 1, 1}, {512, 2, 1}, {640, 2, 1}, {512, 3, 1}, {384, 1, 2}};
+constexpr int kNumShapes = 5;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
 constexpr uint32_t kResSum = 256;                    // residual: threads adding up a large scene's chunks
@@ -437,8 +439,8 @@ __device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
 // solved and synchronised; each thread then gathers both sides of its
 // kPerThread contacts (through L2) before solving any of them (contacts of
 // one colour touch disjoint particles).
-template <int kPgsThreads, int kPerThread>
-__global__ void __launch_bounds__(kPgsThreads, 1) k_pgs(DevPtrs d, SolveArgs a) {
+template <int kPgsThreads, int kPerThread, int kMinBlocks>
+__global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, SolveArgs a) {
   constexpr uint32_t kWave = kPgsThreads * kPerThread;  // contacts per wave
   constexpr size_t kStageBytes = stage_bytes(kWave);
   if (step_failed(d)) return;
@@ -1033,9 +1035,11 @@ int tds_launch_predict(const DevPtrs &d, const StepConsts &k, cudaStream_t st) {
 using PgsKernel = void (*)(DevPtrs, SolveArgs);
 template <int I>
 constexpr PgsKernel pgs_kernel() {
-  return k_pgs<kShapes[I][0], kShapes[I][1]>;
+  return k_pgs<kShapes[I][0], kShapes[I][1], kShapes[I][2]>;
 }
-const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>(), pgs_kernel<2>(), pgs_kernel<3>()};
+const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>(), pgs_kernel<2>(), pgs_kernel<3>(),
+                                           pgs_kernel<4>()};
+int g_pgs_occupancy[kNumShapes];  // co-resident CTAs per SM of each shape (tds_pgs_setup)
 
 int tds_pgs_shapes() { return kNumShapes; }
 void tds_pgs_shape(int i, int *threads, int *per_thread) {
@@ -1078,10 +1082,14 @@ int tds_pgs_setup() {
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)kPgsKernels[i], T, smem) != cudaSuccess)
       return 0;
+    g_pgs_occupancy[i] = occ;
     occ_min = i == 0 ? occ : (occ < occ_min ? occ : occ_min);
   }
   return occ_min;
 }
+
+// Co-resident CTAs per SM of compiled shape i (after tds_pgs_setup).
+int tds_pgs_occupancy(int i) { return g_pgs_occupancy[i]; }
 
 int tds_launch_finish(const DevPtrs &d, const StepConsts &k, uint32_t cap, cudaStream_t st) {
   k_writeback<<<grid_for(cap, 256), 256, 0, st>>>(d);

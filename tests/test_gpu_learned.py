@@ -200,3 +200,52 @@ def test_learned_steps_equal_with_and_without_recording(tds):
         g.close()
     for key in ("x", "v", "w"):
         assert np.array_equal(out[0][key], out[1][key]), key
+
+
+def test_shipped_network_saves_sweeps_on_a_held_out_bed(tds):
+    """What the trained network gains: the shipped weights (trained on the
+    new contacts of plain solves of the small and bulldozing beds) on the
+    excavation bed, a workload they never saw, dug by its bucket. Every step
+    is solved to the 1e-4 residual twice from the same saved state, once
+    with the network's initial impulses for the new contacts and once with
+    zero (the previous-step warm start); the trajectory continues from the
+    latter. Both reach the residual; the network needs fewer sweeps in total
+    and in more steps than not."""
+    from paper_2011_00459_gb300 import learned as LR
+
+    scene = S.excavation(seed=3)
+    g = tds.Scene(scene)
+    g.set_tool_pose(S.parked_tool(scene))
+    g.set_solver(30)
+    g.step(150)
+    path = S.tool_path(scene, S.surface_level(g.read_particles()["x"], scene["r"]), seed=3)
+    g.set_solver(3000, 1e-4, 0)
+    g.set_mlp_weights(LR.load_weights())
+    t0 = 0.3 * path.length / path.speed
+    k = 0
+    while k * scene["dt"] < t0:
+        g.set_tool_pose(path(k * scene["dt"]))
+        g.step(1)
+        k += 1
+    prev, learned, res = [], [], []
+    for _ in range(8):
+        saved = g.save_state()
+        g.set_tool_pose(path(k * scene["dt"]))
+        g.set_warm_start(tds.WARM_LEARNED)
+        g.step(1)
+        st = g.stats()
+        learned.append(st["iterations"])
+        res.append(st["residual"])
+        g.load_state(saved)
+        g.set_warm_start(tds.WARM_PREV)
+        g.step(1)
+        st = g.stats()
+        prev.append(st["iterations"])
+        res.append(st["residual"])
+        k += 1
+    g.close()
+    prev, learned = np.array(prev), np.array(learned)
+    print("sweeps to 1e-4 on the held-out bed: previous step", prev.tolist(), "learned", learned.tolist())
+    assert max(res) <= 1e-4
+    assert learned.sum() < prev.sum()
+    assert (learned < prev).sum() > (learned > prev).sum()
