@@ -34,8 +34,8 @@ def _worker(rank, world, port, out):
         n = bench.reduce_sum(1000 * (rank + 1), world, device="cpu")
 
         class A:
-            workload, n, scenes, iters, tol, max_iters, cold, roofline_sweeps, seed = \
-                "small", 0, 0, 0, 1e-4, 2000, False, -1, 7
+            workload, n, scenes, iters, tol, max_iters, cold, roofline_sweeps, seed, recolour_period = \
+                "small", 0, 0, 0, 1e-4, 2000, False, -1, 7, 16
         scene = bench.make_workload(A, rank)
         out.put((rank, ms, n, float(scene["x"][0, 0]), float(scene["x"][5, 1])))
     finally:
