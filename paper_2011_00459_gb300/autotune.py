@@ -65,18 +65,23 @@ def store_cache(key: str, entry: dict, path: str | None = None) -> None:
 
 
 SYNC_MODES = (1, 0)  # neighbour synchronisation, grid barrier
-SHAPES = ((768, 1), (512, 2), (640, 2), (512, 3))  # solver CTA shapes the library compiles
+# solver CTA shapes the library compiles: (threads, contacts per thread, CTAs per SM)
+SHAPES = ((384, 1, 2), (768, 1, 1), (512, 2, 1), (640, 2, 1), (512, 3, 1), (256, 1, 3))
 KEYS = ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads", "pgs_per_thread")
 
 
 def candidates(cfg: dict, sms: int) -> list:
-    """Solver shapes to time first (sync mode x solver CTA shape, the CTA
-    counts kept), the library's defaults first."""
+    """Solver shapes to time first (sync mode x solver CTA shape), the
+    library's defaults first. A shape keeps the default's share of the
+    machine: its CTAs scale with its CTAs per SM."""
     base = {k: cfg[k] for k in KEYS}
+    per_sm = {(t, p): k for t, p, k in SHAPES}
+    k0 = per_sm.get((base["pgs_threads"], base["pgs_per_thread"]), 1)
     out = [base]
     for sync in SYNC_MODES:
-        for t, per in SHAPES:
-            shape = dict(base, pgs_sync=sync, pgs_threads=t, pgs_per_thread=per)
+        for t, per, k in SHAPES:
+            blocks = max(1, min(sms * k, (base["pgs_blocks"] * k) // k0))
+            shape = dict(base, pgs_sync=sync, pgs_threads=t, pgs_per_thread=per, pgs_blocks=blocks)
             if shape not in out:
                 out.append(shape)
     return out
@@ -84,7 +89,7 @@ def candidates(cfg: dict, sms: int) -> list:
 
 def block_candidates(cfg: dict, best: dict) -> list:
     """Fewer solver CTAs on the chosen solver shape."""
-    p = min(cfg["max_pgs_blocks"], max(1, (3 * best["pgs_blocks"]) // 4))
+    p = max(1, (3 * best["pgs_blocks"]) // 4)
     return [dict(best, pgs_blocks=p)] if p != best["pgs_blocks"] else []
 
 
@@ -129,10 +134,13 @@ def tune(sim, steps: int = 3, sweeps: int = 50, use_cache: bool = True, path: st
         hit = load_cache(path).get(key)
         if hit and all(k in hit.get("shape", {}) for k in KEYS):
             shape = hit["shape"]
-            if shape["pgs_blocks"] <= cfg["max_pgs_blocks"] and shape["colour_blocks"] <= cfg["max_colour_blocks"]:
-                g.set_launch_config(**shape)
-                return {"shape": shape, "ms": hit.get("ms"), "source": "cache", "key": key, "sweeps": sweeps,
-                        "steps": 0}
+            if shape["colour_blocks"] <= cfg["max_colour_blocks"]:
+                try:
+                    g.set_launch_config(**shape)  # the library checks the solver CTAs against the shape
+                    return {"shape": shape, "ms": hit.get("ms"), "source": "cache", "key": key, "sweeps": sweeps,
+                            "steps": 0}
+                except Exception:
+                    g.set_launch_config(**{k: cfg[k] for k in KEYS})
     saved = g.solver
     g.set_solver(sweeps, 0.0, 10)
     results = []

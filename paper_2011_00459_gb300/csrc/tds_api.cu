@@ -687,7 +687,8 @@ tds_status create_impl(const tds_scene_desc *descs, uint32_t count, void *worksp
     return fail(TDS_ERR_CUDA, std::string("device query failed: ") + cudaGetErrorString(ce));
   }
   s->sms = sms;
-  s->pgs_blocks = pgs_blocks_for(s->L.n, sms);  // one co-resident CTA per SM at most
+  // the default solver shape's co-resident CTAs at most
+  s->pgs_blocks = pgs_blocks_for(s->L.n, sms * std::max(1, tds_pgs_occupancy(0)));
   s->colour_blocks = sms * (occ_col < 4 ? occ_col : 4);
   s->max_pgs_blocks = 64 * sms;  // the workspace's limit; each shape's co-residency limits it further
   s->max_colour_blocks = sms * occ_col;

@@ -239,8 +239,10 @@ struct SolveArgs {
 // large part of it.
 // (threads, contacts per thread, co-resident CTAs per SM the register budget
 // is sized for)
-constexpr int kShapes[][3] = {{768, 1, 1}, {512, 2, 1}, {640, 2, 1}, {512, 3, 1}, {384, 1, 2}};
-constexpr int kNumShapes = 5;
+// is sized for). The first is the default: two 384-thread CTAs per SM, each
+// with its own neighbours, keep an SM busy while one of them waits.
+constexpr int kShapes[][3] = {{384, 1, 2}, {768, 1, 1}, {512, 2, 1}, {640, 2, 1}, {512, 3, 1}, {256, 1, 3}};
+constexpr int kNumShapes = 6;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
 constexpr uint32_t kResSum = 256;                    // residual: threads adding up a large scene's chunks
@@ -1038,7 +1040,7 @@ constexpr PgsKernel pgs_kernel() {
   return k_pgs<kShapes[I][0], kShapes[I][1], kShapes[I][2]>;
 }
 const PgsKernel kPgsKernels[kNumShapes] = {pgs_kernel<0>(), pgs_kernel<1>(), pgs_kernel<2>(), pgs_kernel<3>(),
-                                           pgs_kernel<4>()};
+                                           pgs_kernel<4>(), pgs_kernel<5>()};
 int g_pgs_occupancy[kNumShapes];  // co-resident CTAs per SM of each shape (tds_pgs_setup)
 
 int tds_pgs_shapes() { return kNumShapes; }

@@ -236,7 +236,8 @@ def test_shipped_network_saves_sweeps_on_a_held_out_bed(tds):
         st = g.stats()
         learned.append(st["iterations"])
         res.append(st["residual"])
-        g.load_state(saved)
+        g.load_state(saved)  # (the state holds the tool pose of the save: set this step's again)
+        g.set_tool_pose(path(k * scene["dt"]))
         g.set_warm_start(tds.WARM_PREV)
         g.step(1)
         st = g.stats()
