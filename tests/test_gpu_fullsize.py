@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2011_00459_gb300 import scenes as S
-from tests.parity_cases import packed_scene, rel_impulse_error
+from tests.parity_cases import packed_scene, per_contact_impulse_error, rel_impulse_error
 
 pytestmark = pytest.mark.gpu
 
@@ -42,6 +42,12 @@ def test_one_million_spheres_one_step(tds, orc):
     assert np.array_equal(out["keys"], ref["keys"])
     assert np.array_equal(out["colour"].astype(np.int64), ref["colour"].astype(np.int64))
     assert rel_impulse_error(out["lam"], ref["lam"]) <= 1e-4
+    # every contact, not only the aggregate: |dLambda| over the contact's weight scale
+    e = per_contact_impulse_error(scene, out["keys"], out["lam"], ref["lam"])
+    print(f"1M spheres, per-contact impulse error / W: 99.9th pct {np.percentile(e, 99.9):.2e}, max {e.max():.2e}; "
+          f"residual gpu {stats['residual']:.6e} oracle {ref['residual']:.6e}")
+    assert np.percentile(e, 99.9) <= 1e-3
+    assert abs(stats["residual"] - ref["residual"]) <= 1e-3 * ref["residual"]
     assert np.abs(parts["x"].astype(np.float64) - st.x).max() <= 1e-6
 
 
@@ -75,6 +81,7 @@ def test_256_beds_one_batch_graph_replay(tds, orc):
         assert np.array_equal(keys, ref["keys"]), q
         assert np.array_equal(col.astype(np.int64), ref["colour"].astype(np.int64)), q
         assert rel_impulse_error(lam, ref["lam"]) <= 1e-4, q
+        assert np.percentile(per_contact_impulse_error(bed, keys, lam, ref["lam"]), 99.9) <= 1e-3, q
         assert np.abs(xs[q].astype(np.float64) - st.x).max() <= 1e-6, q
 
 
