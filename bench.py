@@ -85,7 +85,7 @@ def parse():
     ap.add_argument("--pgs-sync", type=int, default=-1, choices=[-1, 0, 1],
                     help="solver sync between colours: 1 neighbour, 0 grid barrier (-1: library default)")
     ap.add_argument("--pgs-blocks", type=int, default=0, help="solver CTAs (0: library default)")
-    ap.add_argument("--pgs-shape", default="", help="solver CTA shape THREADSxPER_THREAD (e.g. 384x1)")
+    ap.add_argument("--pgs-shape", default="", help="solver CTA shape THREADSxPER_THREAD (e.g. 416x1)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes (no untimed tuning before warm-up)")
     ap.add_argument("--no-forms", action="store_true",

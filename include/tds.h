@@ -440,9 +440,10 @@ tds_status tds_load_state(tds_scene *s, const void *buf, uint64_t bytes);
  * with the CTAs whose particles it can touch (1, the default) or all CTAs
  * with a grid barrier (0); colour_blocks: persistent colouring CTAs;
  * pgs_threads x pgs_per_thread: the solver CTA's threads and contacts per
- * thread, one of the compiled shapes 768x1 (the default), 512x2, 640x2,
- * 512x3 (one CTA per SM) and 384x1 (two CTAs per SM) (both 0 keep the current
- * shape).
+ * thread, one of the compiled shapes 416x1 (the default, two CTAs per SM),
+ * 768x1, 512x2, 640x2, 512x3 (one CTA per SM) and 256x1 (three CTAs per SM);
+ * in each, the last warp stages the contact rows and the other threads solve
+ * (both 0 keep the current shape).
  * max_pgs_blocks / max_colour_blocks (read only) are the co-resident limits
  * (max_pgs_blocks for the current solver shape; a shape change with
  * pgs_blocks 0 lowers the solver CTAs to the new shape's limit if needed).

@@ -66,7 +66,7 @@ def store_cache(key: str, entry: dict, path: str | None = None) -> None:
 
 SYNC_MODES = (1, 0)  # neighbour synchronisation, grid barrier
 # solver CTA shapes the library compiles: (threads, contacts per thread, CTAs per SM)
-SHAPES = ((384, 1, 2), (768, 1, 1), (512, 2, 1), (640, 2, 1), (512, 3, 1), (256, 1, 3))
+SHAPES = ((416, 1, 2), (768, 1, 1), (512, 2, 1), (640, 2, 1), (512, 3, 1), (256, 1, 3))
 KEYS = ("pgs_blocks", "pgs_sync", "colour_blocks", "pgs_threads", "pgs_per_thread")
 
 

@@ -227,21 +227,21 @@ struct SolveArgs {
   float tol, sig_t, sig_r;
   int apply_warm;
   int sync;  // between colours: 0 grid barrier, 1 neighbour synchronisation
+  uint32_t n;  // particle slots
 };
 
 // ---------------------------------------------------------------------------
 // Staging of the contact rows and impulses with bulk copies (TMA)
 // ---------------------------------------------------------------------------
-// CTA shapes compiled (threads, contacts per thread per wave; a wave is
-// their product); launch configurations choose one by index. Measured on the
-// 1M bed and the batch, one contact per thread over 768 threads is fastest:
-// each colour phase is a latency chain, and a thread's serial updates are a
-// large part of it.
-// (threads, contacts per thread, co-resident CTAs per SM the register budget
-// is sized for)
-// is sized for). The first is the default: two 384-thread CTAs per SM, each
-// with its own neighbours, keep an SM busy while one of them waits.
-constexpr int kShapes[][3] = {{384, 1, 2}, {768, 1, 1}, {512, 2, 1}, {640, 2, 1}, {512, 3, 1}, {256, 1, 3}};
+// CTA shapes compiled: (threads, contacts per thread, co-resident CTAs per
+// SM the register budget is sized for); launch configurations choose one by
+// index. In every shape the last warp stages the waves and the others solve
+// (a wave is (threads - 32) x contacts per thread, see pgs_wave). The first
+// is the default, measured fastest on the 1M bed: two 416-thread CTAs per SM
+// (384 solving threads each, one contact per thread). Each colour phase is a
+// latency chain of which a thread's serial updates are a large part, and the
+// second CTA keeps the SM busy while the first waits.
+constexpr int kShapes[][3] = {{416, 1, 2}, {768, 1, 1}, {512, 2, 1}, {640, 2, 1}, {512, 3, 1}, {256, 1, 3}};
 constexpr int kNumShapes = 6;
 constexpr int kStages = 2;                           // waves in flight
 constexpr uint32_t kFirstCheck = 5;                  // first residual check in adaptive mode
@@ -254,6 +254,11 @@ constexpr size_t kRowBytes = 72;
 constexpr size_t kOffAb = 0, kOffRn = 8, kOffRq = 24, kOffRm = 40, kOffLa = 48, kOffLb = 64;  // x wave size
 __host__ __device__ constexpr size_t stage_bytes(int wave) { return (size_t)wave * kRowBytes; }
 __host__ __device__ constexpr size_t pgs_smem(int wave) { return kStages * stage_bytes(wave); }
+// The last warp of a CTA stages the waves (bulk copies take the issuing
+// thread a long time each: on a computing warp they would hold up every
+// wave's barrier); the other warps solve, one wave = their threads x the
+// contacts per thread.
+__host__ __device__ constexpr int pgs_wave(int threads, int per_thread) { return (threads - 32) * per_thread; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -275,16 +280,21 @@ __device__ __forceinline__ bool mbar_test(unsigned long long *bar, uint32_t pari
   return ok != 0;
 }
 // Bounded wait of one thread for a phase of a stage barrier; false (error
-// latched) when it has waited longer than limit_ns.
+// latched) when it has waited longer than limit_ns, or (if early) at once
+// when the step has already failed. The wait for the copies still in flight
+// before a CTA exits is not early: it gives those copies their full time.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, int32_t *err,
-                                          unsigned long long limit_ns) {
+                                          unsigned long long limit_ns, bool early = true) {
   unsigned long long t0 = 0;
   for (unsigned k = 0;; ++k) {
     if (mbar_test(bar, parity)) return true;
     if (k == 0) t0 = global_ns();
-    if ((k & 15u) == 15u && global_ns() - t0 > limit_ns) {
-      latch_error(err, DEV_ERR_BARRIER);
-      return false;
+    if ((k & 15u) == 15u) {
+      if (early && *(volatile int32_t *)err != 0) return false;  // the step has failed already
+      if (global_ns() - t0 > limit_ns) {
+        latch_error(err, DEV_ERR_BARRIER);
+        return false;
+      }
     }
   }
 }
@@ -443,7 +453,9 @@ __device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
 // one colour touch disjoint particles).
 template <int kPgsThreads, int kPerThread, int kMinBlocks>
 __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, SolveArgs a) {
-  constexpr uint32_t kWave = kPgsThreads * kPerThread;  // contacts per wave
+  constexpr uint32_t kCompute = kPgsThreads - 32;      // solving threads; the last warp stages
+  constexpr uint32_t kProducer = kCompute;             // the staging thread (lane 0 of the last warp)
+  constexpr uint32_t kWave = pgs_wave(kPgsThreads, kPerThread);  // contacts per wave
   constexpr size_t kStageBytes = stage_bytes(kWave);
   if (step_failed(d)) return;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -557,12 +569,12 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
     }
   }
 
-  // producer (thread 0): the next wave to stage
+  // producer (thread kProducer): the next wave to stage
   uint32_t issued = 0, consumed = 0;
   WaveSeq prod{0, 0, 0xFFFFFFFFu};
   if (waves_per_sweep > 0 && a.max_iters > 0) {
     prod.advance(s_nw, ncol, a.max_iters);  // first wave
-    if (threadIdx.x == 0)
+    if (threadIdx.x == kProducer)
       for (uint32_t k = 0; k < ahead && prod.valid(a.max_iters); ++k) {
         issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
                    &full[issued % kStages], kWave);
@@ -590,7 +602,14 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         unsigned char *stage = smem + (size_t)st * kStageBytes;
         // a wait for this CTA's own bulk copies (which complete in
         // microseconds): the fixed limit, not the limit on waits for others
-        if (!mbar_wait(&full[st], (consumed / kStages) & 1u, d.err, TDS_BARRIER_NS)) { ok = false; break; }
+        // A wait that gives up (the error is latched) skips this wave, and no
+        // thread leaves the loop here: every CTA leaves it together at the
+        // next residual check, whose grid barrier sees the error. Until then
+        // a stage may be refilled while an old copy still lands in it, so
+        // every particle index read from a stage is checked against the
+        // particle count before use.
+        const bool staged =
+            threadIdx.x < kCompute && mbar_wait(&full[st], (consumed / kStages) & 1u, d.err, TDS_BARRIER_NS);
         const uint2 *sab = reinterpret_cast<const uint2 *>(stage + kOffAb * kWave);
         const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
         const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);
@@ -605,11 +624,12 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         // gathers of every contact of this thread first (disjoint particles)
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
-          const uint32_t li = j * kPgsThreads + threadIdx.x;
-          gp[j] = li < q.n1 ? q.a1 + li : (li >= q.n1e && li < q.n1e + q.n2 ? q.a2 + (li - q.n1e) : ~0u);
+          const uint32_t li = j * kCompute + threadIdx.x;
+          gp[j] = !staged ? ~0u
+                  : li < q.n1 ? q.a1 + li : (li >= q.n1e && li < q.n1e + q.n2 ? q.a2 + (li - q.n1e) : ~0u);
           if (gp[j] != ~0u) {
             const uint2 ab = sab[li];
-            if (ab.x != 0xFFFFFFFFu) {  // not a padding slot
+            if (ab.x < a.n && (!is_dyn(ab.y) || ab.y < a.n)) {  // not a padding slot (all ones)
               if (skip_done) qs[j] = __ldcg(d.sid + ab.x);
               A[j] = load_side(d, ab.x);
               if (is_dyn(ab.y)) B[j] = load_side(d, ab.y);
@@ -619,11 +639,11 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         }
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) {
-          const uint32_t li = j * kPgsThreads + threadIdx.x;
+          const uint32_t li = j * kCompute + threadIdx.x;
           if (gp[j] != ~0u) {
             Row r;
             r.ab = sab[li];
-            if (r.ab.x == 0xFFFFFFFFu) continue;
+            if (r.ab.x >= a.n || (is_dyn(r.ab.y) && r.ab.y >= a.n)) continue;  // padding slot
             if (skip_done && scene_done(s_done, qs[j])) continue;  // its scene met the tolerance
             const float4 rn = srn[li], rq = srq[li];
             const float2 rm = srm[li];
@@ -644,7 +664,7 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();  // the stage is free again
         ++consumed;
-        if (threadIdx.x == 0 && prod.valid(a.max_iters)) {
+        if (threadIdx.x == kProducer && prod.valid(a.max_iters)) {
           issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
                      &full[issued % kStages], kWave);
           ++issued;
@@ -784,9 +804,9 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
   }
   // drain the waves still in flight before the CTA exits (bulk copies of this
   // CTA's own: a fixed, generous limit, whatever the limit on waits for others)
-  if (threadIdx.x == 0)
+  if (threadIdx.x == kProducer)
     for (uint32_t q = consumed; q < issued; ++q)
-      if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err, TDS_BARRIER_NS)) break;
+      if (!mbar_wait(&full[q % kStages], (q / kStages) & 1u, d.err, TDS_BARRIER_NS, false)) break;
   const bool all_ok = __syncthreads_and(ok) != 0;  // every thread of the CTA reaches this point
   if (blockIdx.x == 0 && all_ok) {
     // statistics: the sweeps done (the most any scene did), the largest final
@@ -1051,14 +1071,14 @@ void tds_pgs_shape(int i, int *threads, int *per_thread) {
 
 cudaError_t tds_launch_pgs(const DevPtrs &d, const StepConsts &k, uint32_t max_iters, float tol,
                            uint32_t every, int apply_warm, int blocks, int sync, int shape, cudaStream_t st) {
-  SolveArgs a{max_iters, every, tol, k.sig_t, k.sig_r, apply_warm, sync};
+  SolveArgs a{max_iters, every, tol, k.sig_t, k.sig_r, apply_warm, sync, k.n};
   cudaMemsetAsync(d.bar, 0, 2 * sizeof(uint32_t), st);
   if (sync) cudaMemsetAsync(d.prog, 0, sizeof(uint32_t) * kProgStride * (size_t)blocks, st);
   DevPtrs dd = d;
   void *args[] = {&dd, &a};
   const int T = kShapes[shape][0];
   return cudaLaunchCooperativeKernel((const void *)kPgsKernels[shape], dim3(blocks), dim3(T), args,
-                                     pgs_smem(T * kShapes[shape][1]), st);
+                                     pgs_smem(pgs_wave(T, kShapes[shape][1])), st);
 }
 
 cudaError_t tds_launch_impact(const DevPtrs &d, const StepConsts &k, float e, float vimp, uint32_t iters,
@@ -1077,7 +1097,7 @@ int tds_pgs_setup() {
   int occ_min = 0;
   for (int i = 0; i < kNumShapes; ++i) {
     const int T = kShapes[i][0];
-    const size_t smem = pgs_smem(T * kShapes[i][1]);
+    const size_t smem = pgs_smem(pgs_wave(T, kShapes[i][1]));
     if (cudaFuncSetAttribute((const void *)kPgsKernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return 0;

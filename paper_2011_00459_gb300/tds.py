@@ -38,7 +38,7 @@ EXPORTED = ["tds_workspace_bytes", "tds_create_scene", "tds_set_tool_pose", "tds
             "tds_set_recolour_period"]
 
 WARM_COLD, WARM_PREV, WARM_LEARNED = 0, 1, 2
-SHAPES = ((384, 1), (768, 1), (512, 2), (640, 2), (512, 3), (256, 1))  # solver CTA shapes compiled (threads, contacts per thread)
+SHAPES = ((416, 1), (768, 1), (512, 2), (640, 2), (512, 3), (256, 1))  # solver CTA shapes compiled (threads, contacts per thread)
 
 
 class TdsError(RuntimeError):

@@ -36,7 +36,7 @@ def test_cache_round_trip_and_bad_files(tmp_path, monkeypatch):
 
 def test_candidates_start_with_the_defaults_and_stay_in_limits():
     cfg = {"pgs_blocks": 304, "pgs_sync": 1, "colour_blocks": 608, "max_pgs_blocks": 304,
-           "max_colour_blocks": 1216, "pgs_threads": 384, "pgs_per_thread": 1}
+           "max_colour_blocks": 1216, "pgs_threads": 416, "pgs_per_thread": 1}
     c = A.candidates(cfg, 152)
     assert c[0] == {k: cfg[k] for k in A.KEYS}
     assert len(c) == len({tuple(sorted(x.items())) for x in c})
