@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
   __shared__ double s_rn[kResSum], s_rd[kResSum];
   static_assert(kPgsThreads >= (int)kResSum, "the residual sum needs kResSum threads");
   __shared__ uint32_t s_mn[kPgsThreads / 32], s_mx[kPgsThreads / 32];
-  __shared__ int s_flag, s_fail;
+  __shared__ int s_flag, s_fail, s_gaveup;
   __shared__ uint32_t s_waves, s_jlo, s_jhi;
   __shared__ uint32_t s_done[TDS_MAX_SCENES / 32], s_done_new[TDS_MAX_SCENES / 32];
   __shared__ uint32_t s_rmax, s_ndone, s_ndone_check;
@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
   if (threadIdx.x == 0) {
     s_waves = 0;
     s_fail = 0;
+    s_gaveup = 0;  // a wait for a staged wave gave up
     s_jlo = s_jhi = blockIdx.x;
     s_ndone = 0;
     s_acc[0] = s_acc[1] = 0ull;
@@ -604,12 +605,12 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         // microseconds): the fixed limit, not the limit on waits for others
         // A wait that gives up (the error is latched) skips this wave, and no
         // thread leaves the loop here: every CTA leaves it together at the
-        // next residual check, whose grid barrier sees the error. Until then
-        // a stage may be refilled while an old copy still lands in it, so
-        // every particle index read from a stage is checked against the
-        // particle count before use.
+        // next residual check, whose grid barrier sees the error. The CTA
+        // stages no wave after it; particle indices read from a stage are
+        // checked against the particle count all the same.
         const bool staged =
             threadIdx.x < kCompute && mbar_wait(&full[st], (consumed / kStages) & 1u, d.err, TDS_BARRIER_NS);
+        if (!staged && threadIdx.x < kCompute) s_gaveup = 1;  // read by the staging thread after the barrier
         const uint2 *sab = reinterpret_cast<const uint2 *>(stage + kOffAb * kWave);
         const float4 *srn = reinterpret_cast<const float4 *>(stage + kOffRn * kWave);
         const float4 *srq = reinterpret_cast<const float4 *>(stage + kOffRq * kWave);
@@ -664,7 +665,9 @@ __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, Solv
         asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();  // the stage is free again
         ++consumed;
-        if (threadIdx.x == kProducer && prod.valid(a.max_iters)) {
+        // (no more waves once a wait of this CTA has given up: its stage may
+        // still have a copy landing in it)
+        if (threadIdx.x == kProducer && prod.valid(a.max_iters) && !*(volatile int *)&s_gaveup) {
           issue_wave(d, prod, s_lo, s_hi, smem + (size_t)(issued % kStages) * kStageBytes,
                      &full[issued % kStages], kWave);
           ++issued;
