@@ -409,12 +409,14 @@ __device__ __forceinline__ void issue_wave(const DevPtrs &d, const WaveSeq &q, c
 // particle before phase t then comes from a neighbour that has finished it,
 // and no neighbour can still be reading a particle this CTA writes, so the
 // result equals the grid-barrier order bit for bit. The least advanced CTA
-// never waits, so the scheme cannot deadlock. Each thread polls one
-// neighbour; waits are bounded like grid_barrier.
+// never waits, so the scheme cannot deadlock. The threads poll the
+// neighbours between them; waits are bounded like grid_barrier.
 __device__ __forceinline__ bool neighbour_wait(const DevPtrs &d, uint32_t jlo, uint32_t jhi, uint32_t target,
                                                int *s_fail) {
-  const uint32_t j = jlo + threadIdx.x;
-  if (j <= jhi && j != blockIdx.x) {
+  // thread t polls neighbours jlo + t, jlo + t + blockDim.x, ... (a range can
+  // be wider than the CTA when few contacts of a colour spread over the bed)
+  for (uint32_t j = jlo + threadIdx.x; j <= jhi; j += blockDim.x) {
+    if (j == blockIdx.x) continue;
     unsigned long long t0 = 0;
     for (unsigned spins = 0;; ++spins) {
       uint32_t cur;
@@ -431,6 +433,7 @@ __device__ __forceinline__ bool neighbour_wait(const DevPtrs &d, uint32_t jlo, u
         }
       }
     }
+    if (*(volatile int *)s_fail) break;
   }
   __syncthreads();
   return *s_fail == 0;

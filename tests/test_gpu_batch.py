@@ -203,12 +203,20 @@ def test_launch_shapes_give_identical_results(tds, graph, solver):
     shapes = [dict(pgs_sync=1), dict(pgs_sync=0), dict(pgs_sync=1, pgs_blocks=7, colour_blocks=13),
               dict(pgs_sync=0, pgs_blocks=3), dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=3),
               dict(pgs_sync=1, pgs_threads=512, pgs_per_thread=2, pgs_blocks=5),
-              dict(pgs_sync=0, pgs_threads=640, pgs_per_thread=2)]
+              dict(pgs_sync=0, pgs_threads=640, pgs_per_thread=2),
+              # three CTAs per SM: more CTAs than threads per CTA, so a CTA's
+              # neighbour range can be wider than its threads
+              dict(pgs_sync=1, pgs_threads=256, pgs_per_thread=1, pgs_blocks="max")]
     out = []
     for shape in shapes:
         b = tds.Batch(beds, stream=torch.cuda.Stream())
         b.set_graph(graph)
-        b.set_launch_config(**shape)
+        if shape.get("pgs_blocks") == "max":  # every co-resident CTA of the shape
+            b.set_launch_config(**dict(shape, pgs_blocks=0))
+            b.set_launch_config(**dict(shape, pgs_blocks=b.launch_config()["max_pgs_blocks"]))
+            assert b.launch_config()["pgs_blocks"] > shape["pgs_threads"]
+        else:
+            b.set_launch_config(**shape)
         b.set_tool_poses([S.parked_tool(s) for s in beds])
         b.set_solver(40, 1e-9, 5)
         b.step(6)
