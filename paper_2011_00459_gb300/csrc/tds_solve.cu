@@ -447,13 +447,14 @@ __device__ __forceinline__ void publish(const DevPtrs &d, uint32_t t) {
                  : "memory");
 }
 
-// The persistent solver: one CTA per SM; between colours either a grid
-// barrier or neighbour synchronisation. The rows and impulses of each wave
-// (up to kWave contacts of one segment) are staged in shared memory by bulk
-// copies issued ahead, so they stream from HBM while earlier colours are
-// solved and synchronised; each thread then gathers both sides of its
-// kPerThread contacts (through L2) before solving any of them (contacts of
-// one colour touch disjoint particles).
+// The persistent solver: kMinBlocks co-resident CTAs per SM; between colours
+// either a grid barrier or neighbour synchronisation. The rows and impulses
+// of each wave (up to kWave contacts of one segment) are staged in shared
+// memory by bulk copies that the CTA's last warp issues ahead, so they stream
+// from HBM while earlier colours are solved and synchronised; each solving
+// thread then gathers both sides of its kPerThread contacts (through L2)
+// before solving any of them (contacts of one colour touch disjoint
+// particles).
 template <int kPgsThreads, int kPerThread, int kMinBlocks>
 __global__ void __launch_bounds__(kPgsThreads, kMinBlocks) k_pgs(DevPtrs d, SolveArgs a) {
   constexpr uint32_t kCompute = kPgsThreads - 32;      // solving threads; the last warp stages
