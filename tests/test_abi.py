@@ -142,3 +142,31 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for field, _ in cls._fields_:
             assert got[(cname, field)] == getattr(cls, field).offset, (cname, field)
+
+
+def test_solver_shapes_agree_everywhere():
+    """The solver CTA shapes the library compiles (tds_solve.cu), the
+    binding's and the tuner's lists and the header's documentation name the
+    same shapes, the first being the default; every shape's staged wave keeps
+    the bulk copies 16-byte aligned and fits in shared memory."""
+    from paper_2011_00459_gb300 import autotune, tds
+
+    src = open(os.path.join(ROOT, "paper_2011_00459_gb300", "csrc", "tds_solve.cu")).read()
+    m = re.search(r"constexpr int kShapes\[\]\[3\] = \{(.*?)\};", src, flags=re.S)
+    compiled = [tuple(int(v) for v in t) for t in re.findall(r"\{(\d+),\s*(\d+),\s*(\d+)\}", m.group(1))]
+    assert [s[:2] for s in compiled] == list(tds.SHAPES)
+    assert compiled == [tuple(s) for s in autotune.SHAPES]
+    header = open(os.path.join(ROOT, "include", "tds.h")).read()
+    doc = re.sub(r"\s+", " ", header[header.index("pgs_threads x pgs_per_thread"):][:400])
+    for t, p, _ in compiled:
+        assert f"{t}x{p}" in doc, (t, p)
+    assert f"{compiled[0][0]}x{compiled[0][1]} (the default" in doc
+    row = int(re.search(r"constexpr size_t kRowBytes = (\d+);", src).group(1))
+    offs = [int(v) for v in re.findall(r"kOff[A-Za-z]+ = (\d+)", src)]
+    stages = int(re.search(r"constexpr int kStages = (\d+);", src).group(1))
+    for t, p, ctas in compiled:
+        wave = (t - 32) * p  # the last warp stages, the others solve
+        assert all(o * wave % 16 == 0 for o in offs) and row * wave % 128 == 0, (t, p)
+        dyn = stages * row * wave
+        assert dyn + 8192 <= 227 * 1024, (t, p)  # per CTA, beside the static shared memory
+        assert ctas * (dyn + 8192) <= 228 * 1024, (t, p)  # the CTAs an SM holds
